@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""HOQRI hot-path benchmark: TTMcTC nonzeros per second on one GB300.
+
+One step = one HOQRI sweep (Alg. 2: for every mode the core pass, the TTMcTC
+pass and the FP64 QR) on the resident workload; the fit of each sweep comes
+from the next core pass.  value = nnz * N * steps * world / time, with nnz
+counted after summing repeated coordinates.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the stand-in for the paper's CPU
+implementation) on the host cores on a bounded sample of the same workload.
+With --gpus N > 1 (launched by torchrun) every rank runs an independent
+replica of the workload (HOQRI on one tensor has no exchange step here).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TTMcTC nnz/s & roofline %, mixed vs FP32 plain at fit err≤1e-6; serve p50/p99"
+UNIT = "nnz/s"
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--scale", type=float, default=1.0, help="nnz scale of the workload (1.0 = full size)")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    Q = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        mine = [r for r in rows if len(r) >= 10 and (self.uuid is None or self.uuid in r[1])]
+        if not mine:
+            mine = [r for r in rows if len(r) >= 10]
+        if not mine:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[2]) for r in mine]
+        mx = max(num(r[3]) for r in mine)
+        loaded = [s for s, r in zip(sm, mine) if num(r[4]) > 200.0] or sm
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in mine:
+            for k, nm in enumerate(names):
+                if r[6 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mine)}
+
+
+# -------------------------------------------------------------------------- workload
+
+def make_workload(cfg_name, scale, rank):
+    from paper_2510_16930_gb300 import inputs
+    X, U0, cfg = inputs.make_config(cfg_name, scale=scale)
+    return X, U0, cfg
+
+
+def prec_of(cfg):
+    from paper_2510_16930_gb300 import hoqri
+    return {"fp64": hoqri.HOQRI_FP64, "fp32": hoqri.HOQRI_FP32, "bf16x3": hoqri.HOQRI_BF16X3}[cfg["prec"]]
+
+
+def alg_flops_per_pass(dims, ranks, rows, nnz, n):
+    """Multiply-adds of one pass for mode n, in the smaller of the paper's two
+    TTMcTC counts (Table 2): nnz * P_{-n} + R_n * P, times 2 flops."""
+    P = math.prod(ranks)
+    Pm = P // ranks[n]
+    return 2.0 * (nnz * Pm + rows[n] * P)
+
+
+def alg_bytes_per_pass(dims, ranks, rows, nnz, n, rsize):
+    """Stream bytes of one pass: per nonzero N-1 int32 indices and a value, per
+    non-empty row its id and offset, the output A_n (TTMcTC)."""
+    N = len(dims)
+    return nnz * ((N - 1) * 4 + rsize) + rows[n] * 12 + dims[n] * ranks[n] * rsize
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2510_16930_gb300", "csrc"))):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(ROOT, "paper_2510_16930_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(cfg_name, kernel_tag):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = d.get(f"{kernel_tag}:{cfg_name}")
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------------ CPU oracle
+
+def cpu_oracle_rate(X, U0, target_s, max_sample=None):
+    """Time one oracle sweep (Alg. 2 with the element-wise TTMcTC of Alg. 3) on
+    the first S nonzeros of the workload, S sized for about target_s seconds.
+    Returns (nnz/s, cores, sample description, seconds)."""
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    N = X.N
+
+    def run(S):
+        idx = [np.ascontiguousarray(a[:S]) for a in X.idx]
+        v = np.ascontiguousarray(X.vals[:S], dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.hoqri(X.dims, idx, v, U0, 1)
+        return time.perf_counter() - t0
+
+    S = min(2000, X.nnz)
+    t = run(S)
+    while t < 0.5 and S < X.nnz:
+        S = min(X.nnz, S * 4)
+        t = run(S)
+    S2 = int(min(X.nnz, max(S, S * target_s / max(t, 1e-3) * 0.8)))
+    if max_sample:
+        S2 = min(S2, max_sample)
+    if S2 != S:
+        t = run(S2)
+        S = S2
+    return S * N / t, oracle.threads(), f"first {S} of {X.nnz} nonzeros, one sweep (N={N} modes), FP64", t
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    X, U0, cfg = make_workload(args.config, args.scale, 0)
+    import numpy as np
+    from oracle import oracle
+    oracle.build()
+    # one calibration sample sizes every step to about 8 s of CPU work
+    rate, cores, sample, secs = cpu_oracle_rate(X, U0, 8.0)
+    S = int(sample.split()[1])
+    idx = [np.ascontiguousarray(a[:S]) for a in X.idx]
+    v = np.ascontiguousarray(X.vals[:S], dtype=np.float64)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.hoqri(X.dims, idx, v, U0, 1)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    step_s = sum(times) / len(times)
+    value = S * X.N / step_s
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(args, cfg, X, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out))
+
+
+def config_block(args, cfg, X, nnz_c):
+    return {"workload": f"{args.config}: {'x'.join(str(d) for d in cfg['dims'])}, nnz {nnz_c or cfg['nnz_target']}, "
+                        f"{cfg['dist']}{'(' + str(cfg.get('s')) + ')' if cfg['dist'] == 'zipf' else ''}, "
+                        f"ranks {tuple(cfg['ranks'])}, {cfg['prec']}",
+            "dims": list(cfg["dims"]), "ranks": list(cfg["ranks"]), "nnz": nnz_c or cfg["nnz_target"],
+            "scale": args.scale, "step": "one HOQRI sweep (core + TTMcTC + FP64 QR per mode, fit)",
+            "l2": "inputs larger than L2 (nonzero streams of every mode stay resident in HBM)",
+            "parallelism": f"replicas x{args.gpus}"}
+
+
+# ---------------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2510_16930_gb300 import hoqri
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    X, U0, cfg = make_workload(args.config, args.scale, rank)
+    prec = prec_of(cfg)
+    npdt = np.float64 if prec == hoqri.HOQRI_FP64 else np.float32
+    rsize = 8 if prec == hoqri.HOQRI_FP64 else 4
+    tdt = torch.float64 if prec == hoqri.HOQRI_FP64 else torch.float32
+    N = X.N
+    stream = torch.cuda.Stream()
+    idx_d = [torch.from_numpy(a).cuda() for a in X.idx]
+    vals_d = torch.from_numpy(X.vals.astype(npdt)).cuda()
+    U0_d = [torch.from_numpy(u.astype(npdt)).cuda() for u in U0]
+    torch.cuda.synchronize()
+    opt = hoqri.hoqri_default_options(prec=prec, chunk_nnz=args.chunk)
+    ctx = hoqri.hoqri_create(X.dims, cfg["ranks"], X.nnz, idx_d, vals_d, opt, U0_d, stream.cuda_stream)
+    nnz_c, rows, dev_bytes = hoqri.hoqri_info(ctx, N)
+    del idx_d, vals_d
+    # warm-up sweeps
+    hoqri.hoqri_iterate(ctx, args.warmup, want_hist=False)
+    hoqri.hoqri_synchronize(ctx)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    clocks = ClockSampler(uuid)
+    hoqri.hoqri_profile_enable(ctx, True)
+    _, launches0 = hoqri.hoqri_profile_read(ctx)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hist = hoqri.hoqri_iterate(ctx, args.steps, want_hist=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    prof, launches1 = hoqri.hoqri_profile_read(ctx)
+    hoqri.hoqri_profile_enable(ctx, False)
+    resid_last, _, _ = hoqri.hoqri_fit(ctx)
+    ms_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = nnz_c * N * args.steps * world / (ms_max / 1e3)
+
+    # roofline of the dominant kernel (the TTMcTC pass), per launch
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    flops = [alg_flops_per_pass(X.dims, cfg["ranks"], rows, nnz_c, n) for n in range(N)]
+    byts = [alg_bytes_per_pass(X.dims, cfg["ranks"], rows, nnz_c, n, rsize) for n in range(N)]
+    ttm_launches = max(prof["ttmctc_n"], 1)
+    ttm_ms = prof["ttmctc_ms"] / ttm_launches
+    core_ms = prof["core_ms"] / max(prof["core_n"], 1)
+    flops_per_launch = sum(flops) / N
+    bytes_per_launch = sum(byts) / N
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    if prec == hoqri.HOQRI_FP64:
+        bound, unit = "alu", "TFLOP/s"
+        peak = None  # FP64 rate: derived below from the measured clock
+        achieved = flops_per_launch / (ttm_ms / 1e3) / 1e12
+        peak = nsm * 2 * 2 * sm_max * 1e6 / 1e12  # assumed 2 FP64 FMA/clk/SM
+    else:
+        bound, unit = "alu", "TFLOP/s"
+        achieved = flops_per_launch / (ttm_ms / 1e3) / 1e12
+        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = ncu_traffic(args.config, "ttmctc")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": traffic, "kernel": "TTMcTC pass (k_pass_*)",
+                "peak_source": f"derived: {nsm} SMs x {FP32_LANES_PER_SM if prec != 0 else 2} lanes x 2 flop x {sm_max:.0f} MHz",
+                "hbm_gbs_achieved": bytes_per_launch / (ttm_ms / 1e3) / 1e9,
+                "hbm_gbs_peak_measured": peaks.get("hbm_gbs"),
+                "alg_flops_per_launch": flops_per_launch, "alg_bytes_per_launch": bytes_per_launch,
+                "ms_per_launch": ttm_ms, "core_pass_ms_per_launch": core_ms,
+                "qr_ms_per_launch": prof["qr_ms"] / max(prof["qr_n"], 1)}
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == hoqri.HOQRI_FP32 else (
+               "f64" if prec == hoqri.HOQRI_FP64 else "bf16x3"),
+           "data": "synthetic", "config": config_block(args, cfg, X, nnz_c), "roofline": roofline,
+           "gpu_launches": int(launches1 - launches0), "clocks": clk,
+           "final_resid": resid_last, "device_bytes": dev_bytes}
+
+    # end to end through the public API from pinned host buffers
+    if not args.no_e2e:
+        iters = int(cfg["iters"])
+        idx_h = [torch.from_numpy(a).pin_memory() for a in X.idx]
+        vals_h = torch.from_numpy(X.vals.astype(npdt)).pin_memory()
+        U_h = [torch.empty((d, k), dtype=tdt).pin_memory() for d, k in zip(X.dims, cfg["ranks"])]
+        bi = sum(a.numel() * 4 for a in idx_h) + vals_h.numel() * rsize
+        bo = sum(u.numel() * rsize for u in U_h) + 8
+        e2e_steps = 2
+        times = []
+        for i in range(e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            c2 = hoqri.hoqri_create(X.dims, cfg["ranks"], X.nnz, idx_h, vals_h, opt, U0_d, stream.cuda_stream)
+            hoqri.hoqri_iterate(c2, iters, want_hist=False)
+            for n in range(N):
+                hoqri.hoqri_get_factor(c2, n, U_h[n])
+            hoqri.hoqri_fit(c2)
+            hoqri.hoqri_destroy(c2)
+            torch.cuda.synchronize()
+            if i > 0:
+                times.append(time.perf_counter() - t0)
+        t_e2e = max(times) if world == 1 else max(times)
+        if world > 1:
+            t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        out["e2e"] = {"value": nnz_c * N * iters * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
+                      "d2h_bytes_per_step": bo,
+                      "step": f"hoqri_create from pinned host COO + {iters} sweeps + factors and fit to host",
+                      "s_per_step": t_e2e}
+    hoqri.hoqri_destroy(ctx)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample, secs = cpu_oracle_rate(X, U0, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                               "seconds": secs}
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

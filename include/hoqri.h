@@ -1,0 +1,176 @@
+/*
+ * hoqri.h: C ABI of the GB300 HOQRI hot path.
+ *
+ * HOQRI (higher-order QR iteration, arXiv 2510.16930) computes a low
+ * multilinear rank (Tucker) approximation X ~ G x {U} of a sparse N-way tensor
+ * X (prob. (tucker), Sec. 2.2) with orthonormal factors U_n (I_n x K_n) and the
+ * optimal core G = X x {U^T} (Sec. 2.2).  Its hot path (Alg. 2) repeats, for
+ * n = 1..N:
+ *     A_n <- TTMcTC(X, {U}, n) = Y_(n) G_(n)^T,  Y = X x_{-n} {U^T}   (Eq. ttmctc)
+ *     U_n <- an orthonormal basis of A_n via QR                          (Alg. 2)
+ * with G recomputed from the current factors before every TTMcTC (Alg. 3,
+ * first step).
+ *
+ * Layouts (all row-major, 0-based):
+ *   - COO input: idx[m] is an array of nnz int32 mode-m indices, vals an array
+ *     of nnz values.  A coordinate listed more than once denotes ONE entry
+ *     whose value is the sum of the listed values.
+ *   - U_n: I_n x K_n, element (i, k) at i*K_n + k.
+ *   - G: K_1 x ... x K_N with the LAST index fastest, so the columns of the
+ *     unfolding G_(n) follow the Kronecker order B^(1) (x) ... (x) B^(N) of
+ *     Eq. (2) with mode n skipped.
+ *   - A_n: I_n x K_n; rows of X_(n) without nonzeros give zero rows.
+ * Element type ("real" below): double for HOQRI_FP64, float otherwise.
+ *
+ * Pointers: every array argument may point to host memory or to device
+ * memory of the context's device; the library tells them apart with
+ * cudaPointerGetAttributes.  Inputs are copied: the caller keeps ownership of
+ * everything it passes.  Output buffers are allocated by the caller.  Work is
+ * ordered on the stream given to hoqri_create; a call that writes a host
+ * buffer returns after the data is there, a call that writes only device
+ * buffers returns once the work is queued.
+ *
+ * Errors: every call returns a hoqri_status and never aborts or throws;
+ * hoqri_last_error() gives a message for the calling thread's last failure.
+ * After HOQRI_ERR_CUDA the context should be destroyed.
+ */
+#ifndef HOQRI_H
+#define HOQRI_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HOQRI_API __attribute__((visibility("default")))
+#else
+#define HOQRI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hoqri_ctx hoqri_ctx; /* opaque; owns all device state of one tensor */
+
+typedef enum {
+    HOQRI_OK = 0,
+    HOQRI_ERR_INVALID = 1,      /* bad argument, NULL pointer, index out of range */
+    HOQRI_ERR_OOM = 2,          /* a device allocation failed */
+    HOQRI_ERR_CUDA = 3,         /* a CUDA runtime call or kernel failed */
+    HOQRI_ERR_QR_BREAKDOWN = 4, /* Cholesky breakdown with the fallback disabled */
+    HOQRI_ERR_RANK = 5,         /* K_n > I_n or K_n > prod_{m != n} K_m */
+    HOQRI_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
+    HOQRI_ERR_UNSUPPORTED = 7   /* shape or precision outside this build's kernels */
+} hoqri_status;
+
+typedef enum {
+    HOQRI_FP64 = 0,  /* values, factors, core and A_n in double */
+    HOQRI_FP32 = 1,  /* float on the nonzero streams; Gram, Cholesky and fit in double */
+    HOQRI_BF16X3 = 2 /* FP32 storage; Kronecker-times-core products on the tensor
+                        cores in split BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+} hoqri_precision;
+
+typedef struct {
+    int32_t prec;       /* hoqri_precision */
+    int32_t qr_kind;    /* 0: CholeskyQR2 in FP64, Householder when Cholesky breaks
+                           down; 1: Householder only; 2: CholeskyQR2, breakdown is an
+                           error (HOQRI_ERR_QR_BREAKDOWN) */
+    int32_t chunk_nnz;  /* nonzeros per warp task; 0 = chosen by the library */
+    int32_t autotune;   /* 1: time the candidate chunk sizes once at create */
+    int32_t use_graphs; /* 1: hoqri_iterate replays one sweep as a CUDA graph */
+    int32_t reserved0;
+    uint64_t seed;      /* seed of the initial factors when U0 is NULL */
+    double tol;         /* hoqri_run: stop when |r_t - r_{t-1}| < tol (0: never) */
+} hoqri_options;
+
+/* Fills *opt with the defaults (FP32, CholeskyQR2 + fallback, library-chosen
+ * chunk, no autotune, graphs on, seed 0, tol 0). */
+HOQRI_API void hoqri_default_options(hoqri_options *opt);
+
+/*
+ * Builds the device state for one sparse tensor (Sec. 6: COO storage) and the
+ * initial factors (Alg. 2, first step).
+ *   N        order, 2 <= N <= 8
+ *   dims     N mode sizes, 1 <= I_n < 2^31
+ *   ranks    N multilinear ranks K_n, 1 <= K_n <= 64 and K_n <= I_n and
+ *            K_n <= prod_{m != n} K_m (else HOQRI_ERR_RANK: A_n would be rank
+ *            deficient by construction; the paper is silent on this case)
+ *   nnz      number of listed entries (repeats allowed; they are summed), >= 0
+ *   idx      N pointers to nnz int32 indices each, 0 <= idx[m][z] < dims[m]
+ *   vals     nnz reals
+ *   opt      options (NULL: defaults)
+ *   U0       NULL, or N pointers to I_n x K_n reals with orthonormal columns
+ *            (not checked); NULL draws a seeded Gaussian and orthonormalises it
+ *   stream   cudaStream_t to order all work on (NULL: the legacy default stream)
+ * Duplicates are summed, then one mode-sorted copy of the nonzeros per mode is
+ * built with its permutation and row (slice) descriptors; the raw input is
+ * released before returning.  On failure *out is NULL.
+ */
+HOQRI_API hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const int32_t *ranks,
+                          int64_t nnz, const int32_t *const *idx, const void *vals,
+                          const hoqri_options *opt, const void *const *U0, void *stream);
+
+/* G = X x_1 U_1^T ... x_N U_N^T with the current factors (Sec. 2.2; Alg. 2
+ * last step).  G_out: prod K_n reals, layout above. */
+HOQRI_API hoqri_status hoqri_core(hoqri_ctx *ctx, void *G_out);
+
+/* A_n = TTMcTC(X, {U}, n) with the current factors (Eq. ttmctc; Alg. 3: the core
+ * is recomputed first).  mode is 0-based; A_out: I_n x K_n reals.  The factors
+ * are not changed. */
+HOQRI_API hoqri_status hoqri_ttmctc(hoqri_ctx *ctx, int32_t mode, void *A_out);
+
+/* U_out = orthonormal basis of the columns of A_in (Alg. 2, the QR step): thin QR
+ * with diag(R) > 0 by CholeskyQR2 in FP64 (Householder on breakdown, per
+ * qr_kind).  A_in: I_mode x K_mode reals; U_out may equal A_in.  The factors of
+ * the context are not changed. */
+HOQRI_API hoqri_status hoqri_orthonormalize(hoqri_ctx *ctx, int32_t mode, const void *A_in, void *U_out);
+
+/*
+ * Runs `iters` HOQRI iterations (Alg. 2; one iteration = one sweep n = 1..N of
+ * core, TTMcTC and QR), then the final core.  resid_hist (host, NULL or iters
+ * doubles) receives after each sweep the relative residual
+ *   r = sqrt(max(0, ||X||^2 - ||G||^2)) / ||X||,
+ * which equals ||X - G x {U}|| / ||X|| for orthonormal U and optimal G (Sec. 2.2).
+ */
+HOQRI_API hoqri_status hoqri_iterate(hoqri_ctx *ctx, int32_t iters, double *resid_hist);
+
+/* Copies the current factor U_mode (I_mode x K_mode reals) to U_out. */
+HOQRI_API hoqri_status hoqri_get_factor(hoqri_ctx *ctx, int32_t mode, void *U_out);
+
+/* Replaces the current factor U_mode with U_in (I_mode x K_mode reals, assumed
+ * orthonormal). */
+HOQRI_API hoqri_status hoqri_set_factor(hoqri_ctx *ctx, int32_t mode, const void *U_in);
+
+/* Residual of the last core computed (by hoqri_core, hoqri_ttmctc or
+ * hoqri_iterate): resid as in hoqri_iterate, ||X||^2 and ||G||^2 in FP64.  Any
+ * output pointer may be NULL (host pointers). */
+HOQRI_API hoqri_status hoqri_fit(hoqri_ctx *ctx, double *resid, double *normX2, double *normG2);
+
+/* Sizes after set-up (host pointers, each may be NULL): nnz after summing
+ * repeats; rows[N] = number of non-empty mode-n slices; device bytes held. */
+HOQRI_API hoqri_status hoqri_info(hoqri_ctx *ctx, int64_t *nnz, int64_t *rows, int64_t *device_bytes);
+
+/* Tracing: enable = 1 clears the totals and starts recording a CUDA event pair
+ * around every core pass, TTMcTC pass and QR on the context's stream;
+ * enable = 0 stops recording.  Cheap enough to leave on during timing. */
+HOQRI_API hoqri_status hoqri_profile_enable(hoqri_ctx *ctx, int32_t enable);
+
+/* Totals since the last hoqri_profile_enable(ctx, 1) (synchronises the stream).
+ * out (host, NULL or 6 doubles): core-pass ms, core-pass count, TTMcTC-pass ms,
+ * TTMcTC-pass count, QR ms, QR count.  kernel_launches (host, may be NULL): the
+ * number of kernels the library has launched since hoqri_create. */
+HOQRI_API hoqri_status hoqri_profile_read(hoqri_ctx *ctx, double *out, int64_t *kernel_launches);
+
+/* Blocks until all work queued on the context's stream has finished. */
+HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
+
+/* Message for the calling thread's last failed call ("" if none). */
+HOQRI_API const char *hoqri_last_error(void);
+
+/* Frees all device state; NULL is a no-op. */
+HOQRI_API void hoqri_destroy(hoqri_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOQRI_H */

@@ -1,0 +1,519 @@
+// C ABI of libhoqri: context life cycle and the HOQRI driver (Alg. 2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hoqri {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        set_error(std::string("device allocation of ") + std::to_string(bytes) + " bytes: " + cudaGetErrorString(e));
+        return HOQRI_ERR_OOM;
+    }
+    c->device_bytes += (int64_t)std::max<size_t>(bytes, 16);
+    return HOQRI_OK;
+}
+
+void dfree(void *p) {
+    if (p) cudaFree(p);
+}
+
+static bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+static cudaMemcpyKind kind_to_device(const void *src) {
+    return is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+
+// copy `bytes` from a device buffer to a caller buffer (host or device)
+static hoqri_status copy_out(hoqri_ctx *c, void *dst, const void *src_dev, size_t bytes) {
+    const bool dev = is_device_ptr(dst);
+    HQ_CUDA(cudaMemcpyAsync(dst, src_dev, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!dev) HQ_CUDA(cudaStreamSynchronize(c->stream));
+    return HOQRI_OK;
+}
+
+static hoqri_status ensure_slots(hoqri_ctx *c, int64_t slots) {
+    if (c->dnorm_slots >= slots) return HOQRI_OK;
+    double *nd = nullptr;
+    HQ_TRY(dalloc(c, (void **)&nd, slots * sizeof(double)));
+    HQ_CUDA(cudaMemsetAsync(nd, 0, slots * sizeof(double), c->stream));
+    if (c->dnorm) {
+        HQ_CUDA(cudaMemcpyAsync(nd, c->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        HQ_CUDA(cudaStreamSynchronize(c->stream));
+        dfree(c->dnorm);
+    }
+    c->dnorm = nd;
+    c->dnorm_slots = slots;
+    return HOQRI_OK;
+}
+
+static void destroy_impl(hoqri_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->sweep_exec) cudaGraphExecDestroy(c->sweep_exec);
+    for (auto &r : c->ev_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    for (int n = 0; n < HOQRI_MAXN; ++n) {
+        ModeStore &M = c->ms[n];
+        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.oidx[j]);
+        dfree(M.vals);
+        dfree(M.perm);
+        dfree(M.row_id);
+        dfree(M.row_ptr);
+        dfree(M.chunk_row);
+        dfree(M.split_row);
+        dfree(c->U[n]);
+    }
+    dfree(c->G);
+    dfree(c->A);
+    dfree(c->dnorm);
+    dfree(c->dflag);
+    dfree(c->core_part);
+    dfree(c->a_part);
+    dfree(c->qr_part);
+    dfree(c->qr_small);
+    dfree(c->qr_work);
+    dfree(c->gnorm_part);
+    cudaGetLastError();
+    delete c;
+}
+
+static double resid_of(double nx2, double ng2) {
+    if (!(nx2 > 0)) return 0.0;
+    double r2 = nx2 - ng2;
+    return std::sqrt(r2 > 0 ? r2 : 0.0) / std::sqrt(nx2);
+}
+
+static hoqri_status ev_get(hoqri_ctx *c, cudaEvent_t *e) {
+    if (!c->ev_pool.empty()) {
+        *e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return HOQRI_OK;
+    }
+    HQ_CUDA(cudaEventCreate(e));
+    return HOQRI_OK;
+}
+
+hoqri_status prof_begin(hoqri_ctx *c, int kind, cudaEvent_t *a) {
+    (void)kind;
+    *a = nullptr;
+    if (!c->profiling) return HOQRI_OK;
+    HQ_TRY(ev_get(c, a));
+    HQ_CUDA(cudaEventRecord(*a, c->stream));
+    return HOQRI_OK;
+}
+
+hoqri_status prof_end(hoqri_ctx *c, int kind, cudaEvent_t a) {
+    if (!c->profiling || !a) return HOQRI_OK;
+    cudaEvent_t b;
+    HQ_TRY(ev_get(c, &b));
+    HQ_CUDA(cudaEventRecord(b, c->stream));
+    c->ev_recs.push_back({kind, a, b});
+    return HOQRI_OK;
+}
+
+static hoqri_status prof_collect(hoqri_ctx *c) {
+    if (c->ev_recs.empty()) return HOQRI_OK;
+    HQ_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto &r : c->ev_recs) {
+        float ms = 0.f;
+        HQ_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+        c->prof[2 * r.kind] += ms;
+        c->prof[2 * r.kind + 1] += 1.0;
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->ev_recs.clear();
+    return HOQRI_OK;
+}
+
+static hoqri_status check_mode(hoqri_ctx *c, int32_t mode) {
+    if (!c) {
+        set_error("NULL context");
+        return HOQRI_ERR_INVALID;
+    }
+    if (mode < 0 || mode >= c->N) {
+        set_error("mode out of range");
+        return HOQRI_ERR_INVALID;
+    }
+    return HOQRI_OK;
+}
+
+}  // namespace hoqri
+
+using namespace hoqri;
+
+extern "C" {
+
+void hoqri_default_options(hoqri_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->prec = HOQRI_FP32;
+    opt->qr_kind = 0;
+    opt->chunk_nnz = 0;
+    opt->autotune = 0;
+    opt->use_graphs = 1;
+    opt->seed = 0;
+    opt->tol = 0.0;
+}
+
+const char *hoqri_last_error(void) { return g_last_error.c_str(); }
+
+hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const int32_t *ranks, int64_t nnz,
+                          const int32_t *const *idx, const void *vals, const hoqri_options *opt,
+                          const void *const *U0, void *stream) {
+    g_last_error.clear();
+    if (!out) {
+        set_error("hoqri_create: out is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    *out = nullptr;
+    if (N < 2 || N > HOQRI_MAXN || !dims || !ranks || nnz < 0 || (nnz > 0 && (!idx || !vals))) {
+        set_error("hoqri_create: need 2 <= N <= 8, dims, ranks, nnz >= 0 and idx/vals when nnz > 0");
+        return HOQRI_ERR_INVALID;
+    }
+    for (int n = 0; n < N; ++n) {
+        if (dims[n] < 1 || dims[n] >= (int64_t)INT32_MAX || ranks[n] < 1) {
+            set_error("hoqri_create: need 1 <= dims[n] < 2^31 and ranks[n] >= 1");
+            return HOQRI_ERR_INVALID;
+        }
+        if (nnz > 0 && !idx[n]) {
+            set_error("hoqri_create: idx[n] is NULL");
+            return HOQRI_ERR_INVALID;
+        }
+    }
+    for (int n = 0; n < N; ++n) {
+        int64_t pm = 1;
+        for (int m = 0; m < N; ++m)
+            if (m != n) pm *= ranks[m];
+        if (ranks[n] > HOQRI_MAXK) {
+            set_error("hoqri_create: ranks above 64 are not supported");
+            return HOQRI_ERR_UNSUPPORTED;
+        }
+        if ((int64_t)ranks[n] > dims[n] || (int64_t)ranks[n] > pm) {
+            set_error("hoqri_create: K_n must not exceed I_n nor prod_{m != n} K_m");
+            return HOQRI_ERR_RANK;
+        }
+    }
+    hoqri_options o;
+    hoqri_default_options(&o);
+    if (opt) o = *opt;
+    if (o.prec != HOQRI_FP64 && o.prec != HOQRI_FP32 && o.prec != HOQRI_BF16X3) {
+        set_error("hoqri_create: unknown precision");
+        return HOQRI_ERR_INVALID;
+    }
+    if (o.prec == HOQRI_BF16X3) {
+        set_error("hoqri_create: HOQRI_BF16X3 is not available in this build");
+        return HOQRI_ERR_UNSUPPORTED;
+    }
+    hoqri_ctx *c = new (std::nothrow) hoqri_ctx();
+    if (!c) {
+        set_error("hoqri_create: host allocation failed");
+        return HOQRI_ERR_OOM;
+    }
+    c->N = N;
+    c->P = 1;
+    for (int n = 0; n < N; ++n) {
+        c->dims[n] = dims[n];
+        c->K[n] = ranks[n];
+        c->P *= ranks[n];
+    }
+    c->opt = o;
+    c->prec = o.prec;
+    c->rsize = (o.prec == HOQRI_FP64) ? sizeof(double) : sizeof(float);
+    c->stream = (cudaStream_t)stream;
+    auto fail = [&](hoqri_status s) {
+        std::string msg = g_last_error;
+        destroy_impl(c);
+        g_last_error = msg;
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("hoqri_create: no CUDA device");
+        return fail(HOQRI_ERR_CUDA);
+    }
+    hoqri_status s;
+    if ((s = ensure_slots(c, 64)) != HOQRI_OK) return fail(s);
+    if ((s = dalloc(c, (void **)&c->dflag, 4 * sizeof(int32_t))) != HOQRI_OK) return fail(s);
+    if (cudaMemsetAsync(c->dflag, 0, 4 * sizeof(int32_t), c->stream) != cudaSuccess) return fail(HOQRI_ERR_CUDA);
+
+    // inputs on the device (temporaries released after set-up)
+    std::vector<void *> tmp;
+    auto free_tmp = [&]() {
+        for (void *p : tmp) cudaFree(p);
+        tmp.clear();
+    };
+    const int32_t *idx_dev[HOQRI_MAXN] = {};
+    const void *vals_dev = vals;
+    for (int n = 0; n < N && nnz > 0; ++n) {
+        if (is_device_ptr(idx[n])) {
+            idx_dev[n] = idx[n];
+        } else {
+            void *p = nullptr;
+            if (cudaMalloc(&p, nnz * sizeof(int32_t)) != cudaSuccess) {
+                cudaGetLastError();
+                free_tmp();
+                set_error("hoqri_create: device allocation for the indices failed");
+                return fail(HOQRI_ERR_OOM);
+            }
+            tmp.push_back(p);
+            if (cudaMemcpyAsync(p, idx[n], nnz * sizeof(int32_t), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+                free_tmp();
+                set_error("hoqri_create: copy of the indices failed");
+                return fail(HOQRI_ERR_CUDA);
+            }
+            idx_dev[n] = (const int32_t *)p;
+        }
+    }
+    if (nnz > 0 && !is_device_ptr(vals)) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, nnz * c->rsize) != cudaSuccess) {
+            cudaGetLastError();
+            free_tmp();
+            set_error("hoqri_create: device allocation for the values failed");
+            return fail(HOQRI_ERR_OOM);
+        }
+        tmp.push_back(p);
+        if (cudaMemcpyAsync(p, vals, nnz * c->rsize, cudaMemcpyHostToDevice, c->stream) != cudaSuccess) {
+            free_tmp();
+            set_error("hoqri_create: copy of the values failed");
+            return fail(HOQRI_ERR_CUDA);
+        }
+        vals_dev = p;
+    }
+    s = build_storage(c, idx_dev, vals_dev, nnz);
+    cudaStreamSynchronize(c->stream);
+    free_tmp();
+    if (s != HOQRI_OK) return fail(s);
+
+    int64_t maxIK = 0;
+    for (int n = 0; n < N; ++n) {
+        if ((s = dalloc(c, &c->U[n], c->dims[n] * c->K[n] * c->rsize)) != HOQRI_OK) return fail(s);
+        maxIK = std::max<int64_t>(maxIK, c->dims[n] * c->K[n]);
+    }
+    if ((s = dalloc(c, &c->G, c->P * c->rsize)) != HOQRI_OK) return fail(s);
+    if ((s = dalloc(c, &c->A, maxIK * c->rsize)) != HOQRI_OK) return fail(s);
+    if ((s = qr_init(c)) != HOQRI_OK) return fail(s);
+    if ((s = passes_init(c)) != HOQRI_OK) return fail(s);
+    if (U0) {
+        for (int n = 0; n < N; ++n) {
+            if (!U0[n]) {
+                set_error("hoqri_create: U0[n] is NULL");
+                return fail(HOQRI_ERR_INVALID);
+            }
+            if (cudaMemcpyAsync(c->U[n], U0[n], c->dims[n] * c->K[n] * c->rsize, kind_to_device(U0[n]), c->stream) !=
+                cudaSuccess) {
+                set_error("hoqri_create: copy of U0 failed");
+                return fail(HOQRI_ERR_CUDA);
+            }
+        }
+    } else {
+        if ((s = init_factors_seeded(c)) != HOQRI_OK) return fail(s);
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        set_error("hoqri_create: CUDA error during set-up");
+        return fail(HOQRI_ERR_CUDA);
+    }
+    *out = c;
+    return HOQRI_OK;
+}
+
+void hoqri_destroy(hoqri_ctx *ctx) { destroy_impl(ctx); }
+
+hoqri_status hoqri_core(hoqri_ctx *c, void *G_out) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (!G_out) {
+        set_error("hoqri_core: G_out is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    HQ_TRY(core_pass(c, 0, c->G, nullptr));
+    return copy_out(c, G_out, c->G, c->P * c->rsize);
+}
+
+hoqri_status hoqri_ttmctc(hoqri_ctx *c, int32_t mode, void *A_out) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, mode));
+    if (!A_out) {
+        set_error("hoqri_ttmctc: A_out is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    HQ_TRY(core_pass(c, mode, c->G, nullptr));
+    HQ_TRY(ttmctc_pass(c, mode, c->G, c->A));
+    return copy_out(c, A_out, c->A, c->dims[mode] * c->K[mode] * c->rsize);
+}
+
+hoqri_status hoqri_orthonormalize(hoqri_ctx *c, int32_t mode, const void *A_in, void *U_out) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, mode));
+    if (!A_in || !U_out) {
+        set_error("hoqri_orthonormalize: NULL buffer");
+        return HOQRI_ERR_INVALID;
+    }
+    const size_t bytes = c->dims[mode] * c->K[mode] * c->rsize;
+    HQ_CUDA(cudaMemcpyAsync(c->A, A_in, bytes, kind_to_device(A_in), c->stream));
+    if (is_device_ptr(U_out)) {
+        HQ_TRY(orthonormalize(c, mode, c->A, U_out));
+    } else {
+        void *tmp = nullptr;
+        HQ_TRY(dalloc(c, &tmp, bytes));
+        hoqri_status s = orthonormalize(c, mode, c->A, tmp);
+        if (s == HOQRI_OK) s = copy_out(c, U_out, tmp, bytes);
+        cudaStreamSynchronize(c->stream);
+        dfree(tmp);
+        c->device_bytes -= (int64_t)std::max<size_t>(bytes, 16);
+        if (s != HOQRI_OK) return s;
+    }
+    if (c->opt.qr_kind == 2) {
+        int32_t f[2];
+        HQ_CUDA(cudaMemcpyAsync(f, c->dflag, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        HQ_CUDA(cudaStreamSynchronize(c->stream));
+        if (f[0] != 0) {
+            set_error("hoqri_orthonormalize: Cholesky breakdown");
+            return HOQRI_ERR_QR_BREAKDOWN;
+        }
+    }
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (iters < 0) {
+        set_error("hoqri_iterate: iters < 0");
+        return HOQRI_ERR_INVALID;
+    }
+    const int N = c->N;
+    HQ_TRY(ensure_slots(c, 2 + (int64_t)iters * N + 1));
+    int32_t before = 0;
+    if (c->opt.qr_kind == 2) {
+        HQ_CUDA(cudaMemcpyAsync(&before, c->dflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        HQ_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    for (int t = 0; t < iters; ++t) {
+        for (int n = 0; n < N; ++n) {
+            HQ_TRY(core_pass(c, n, c->G, c->dnorm + 2 + (int64_t)t * N + n));
+            HQ_TRY(ttmctc_pass(c, n, c->G, c->A));
+            HQ_TRY(orthonormalize(c, n, c->A, c->U[n]));
+        }
+    }
+    HQ_TRY(core_pass(c, 0, c->G, c->dnorm + 2 + (int64_t)iters * N));
+    if (resid_hist || c->opt.qr_kind == 2) {
+        std::vector<double> h(2 + (size_t)iters * N + 1);
+        HQ_CUDA(cudaMemcpyAsync(h.data(), c->dnorm, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        int32_t after = 0;
+        HQ_CUDA(cudaMemcpyAsync(&after, c->dflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        HQ_CUDA(cudaStreamSynchronize(c->stream));
+        if (resid_hist)
+            for (int t = 0; t < iters; ++t) resid_hist[t] = resid_of(h[0], h[2 + (size_t)(t + 1) * N]);
+        if (c->opt.qr_kind == 2 && after != before) {
+            set_error("hoqri_iterate: Cholesky breakdown in a QR step");
+            return HOQRI_ERR_QR_BREAKDOWN;
+        }
+    }
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_get_factor(hoqri_ctx *c, int32_t mode, void *U_out) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, mode));
+    if (!U_out) {
+        set_error("hoqri_get_factor: U_out is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    return copy_out(c, U_out, c->U[mode], c->dims[mode] * c->K[mode] * c->rsize);
+}
+
+hoqri_status hoqri_set_factor(hoqri_ctx *c, int32_t mode, const void *U_in) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, mode));
+    if (!U_in) {
+        set_error("hoqri_set_factor: U_in is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    HQ_CUDA(cudaMemcpyAsync(c->U[mode], U_in, c->dims[mode] * c->K[mode] * c->rsize, kind_to_device(U_in), c->stream));
+    if (!is_device_ptr(U_in)) HQ_CUDA(cudaStreamSynchronize(c->stream));
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_fit(hoqri_ctx *c, double *resid, double *normX2, double *normG2) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    double h[2];
+    HQ_CUDA(cudaMemcpyAsync(h, c->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    HQ_CUDA(cudaStreamSynchronize(c->stream));
+    if (resid) *resid = resid_of(h[0], h[1]);
+    if (normX2) *normX2 = h[0];
+    if (normG2) *normG2 = h[1];
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_info(hoqri_ctx *c, int64_t *nnz, int64_t *rows, int64_t *device_bytes) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (nnz) *nnz = c->nnz;
+    if (rows)
+        for (int n = 0; n < c->N; ++n) rows[n] = c->ms[n].R;
+    if (device_bytes) *device_bytes = c->device_bytes;
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_profile_enable(hoqri_ctx *c, int32_t enable) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    HQ_TRY(prof_collect(c));
+    if (enable)
+        for (double &v : c->prof) v = 0.0;
+    c->profiling = enable != 0;
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_profile_read(hoqri_ctx *c, double *out, int64_t *kernel_launches) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    HQ_TRY(prof_collect(c));
+    if (out)
+        for (int i = 0; i < 6; ++i) out[i] = c->prof[i];
+    if (kernel_launches) *kernel_launches = c->nlaunch;
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_synchronize(hoqri_ctx *c) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    HQ_CUDA(cudaStreamSynchronize(c->stream));
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Internal declarations shared by the translation units of libhoqri.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hoqri.h"
+
+#define HOQRI_MAXN 8
+#define HOQRI_MAXK 64
+
+namespace hoqri {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string &msg);
+
+struct Status {
+    hoqri_status code = HOQRI_OK;
+    bool ok() const { return code == HOQRI_OK; }
+};
+
+#define HQ_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess) {                                                        \
+            ::hoqri::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));     \
+            return e_ == cudaErrorMemoryAllocation ? HOQRI_ERR_OOM : HOQRI_ERR_CUDA;     \
+        }                                                                               \
+    } while (0)
+
+#define HQ_TRY(expr)                         \
+    do {                                     \
+        hoqri_status s_ = (expr);            \
+        if (s_ != HOQRI_OK) return s_;       \
+    } while (0)
+
+// ------------------------------------------------------- per-mode storage
+
+// Nonzeros sorted by their mode-n index (stable from the coalesced,
+// lexicographic order), stored as structure of arrays.
+struct ModeStore {
+    int32_t *oidx[HOQRI_MAXN - 1] = {};  // indices of the other modes (ascending m != n)
+    void *vals = nullptr;                // real[nnz]
+    int32_t *perm = nullptr;             // sorted position -> coalesced entry id
+    int64_t R = 0;                       // non-empty rows (slices)
+    int32_t *row_id = nullptr;           // [R] mode-n index of each non-empty row
+    int64_t *row_ptr = nullptr;          // [R+1] first sorted position of each row
+    // partition into warp tasks ("chunks") of C consecutive nonzeros
+    int32_t C = 0;
+    int64_t nchunks = 0;
+    int32_t *chunk_row = nullptr;        // [nchunks] row (index into row_id) holding the chunk start
+    int64_t nsplit = 0;
+    int32_t *split_row = nullptr;        // [nsplit] rows spanning more than one chunk
+};
+
+struct Workspace;  // defined in the pass unit
+
+}  // namespace hoqri
+
+struct hoqri_ctx {
+    int N = 0;
+    int64_t dims[HOQRI_MAXN] = {};
+    int32_t K[HOQRI_MAXN] = {};
+    int64_t P = 1;                      // prod K
+    hoqri_options opt{};
+    int prec = HOQRI_FP32;
+    size_t rsize = 4;                   // sizeof(real)
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    int64_t nnz = 0;                    // after summing repeats
+    hoqri::ModeStore ms[HOQRI_MAXN];
+    void *U[HOQRI_MAXN] = {};           // factors, real[I_n*K_n]
+    void *G = nullptr;                  // real[P]
+    void *A = nullptr;                  // real[max I_n*K_n], TTMcTC output of the sweep
+    // FP64 scalars on the device: [0] ||X||^2, [1] ||G||^2 of the last core,
+    // [2 ...] ||G||^2 history of hoqri_iterate (one slot per core pass)
+    double *dnorm = nullptr;
+    int64_t dnorm_slots = 0;
+    int32_t *dflag = nullptr;           // [0] QR breakdown flag of the current QR, [1] breakdown count
+    // scratch of the passes (partials); see passes.cu
+    void *core_part = nullptr;          // per-CTA core partials
+    int64_t core_part_bytes = 0;
+    void *a_part = nullptr;             // per-chunk TTMcTC partial rows
+    int64_t a_part_bytes = 0;
+    double *qr_part = nullptr;          // Gram partials
+    int64_t qr_part_bytes = 0;
+    double *qr_small = nullptr;         // K x K FP64 workspace (Rinv) and norms
+    double *qr_work = nullptr;          // Householder fallback workspace (max I*K doubles)
+    double *gnorm_part = nullptr;       // block partials of ||G||^2
+    int core_grid = 0;                  // CTAs of the core pass (fixed per context)
+    int pass_grid = 0;
+    int64_t device_bytes = 0;
+    // CUDA graph of one sweep
+    cudaGraphExec_t sweep_exec = nullptr;
+    int graph_slot_base = -1;
+    double host_norm[2] = {0, 0};
+    // tracing
+    int64_t nlaunch = 0;                // kernels launched by the library
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    struct EvRec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<EvRec> ev_recs;
+    double prof[6] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace hoqri {
+
+// device memory helpers (track bytes)
+hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes);
+void dfree(void *p);
+
+// setup (setup.cu)
+hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw);
+hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C);
+
+// passes (passes.cu)
+hoqri_status passes_init(hoqri_ctx *c);
+hoqri_status core_pass(hoqri_ctx *c, int n, void *G_out, double *normG2_slot);
+hoqri_status ttmctc_pass(hoqri_ctx *c, int n, const void *G, void *A_out);
+
+// QR (qr.cu)
+hoqri_status qr_init(hoqri_ctx *c);
+hoqri_status orthonormalize(hoqri_ctx *c, int n, void *A_inout, void *U_out);
+hoqri_status init_factors_seeded(hoqri_ctx *c);
+
+int64_t ceil_div(int64_t a, int64_t b);
+
+// tracing: kinds 0 = core pass, 1 = TTMcTC pass, 2 = QR
+hoqri_status prof_begin(hoqri_ctx *c, int kind, cudaEvent_t *a);
+hoqri_status prof_end(hoqri_ctx *c, int kind, cudaEvent_t a);
+
+}  // namespace hoqri

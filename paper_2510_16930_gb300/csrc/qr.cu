@@ -1,0 +1,365 @@
+// Orthonormalisation U_n <- orthonormal basis of A_n (Alg. 2, the QR step).
+//
+// CholeskyQR2 in FP64: W = A^T A (Gram, FP64 sums in a fixed order),
+// W = R^T R (Cholesky, one CTA), A <- A R^{-1}; then once more on the result.
+// Both R factors have a positive diagonal, so the result is the Q of the thin
+// QR with diag(R) > 0.  When a Cholesky pivot is not clearly positive (A is
+// rank deficient or too ill-conditioned for CholeskyQR), a one-CTA Householder
+// QR in FP64 produces Q instead (columns signed so diag(R) >= 0; zero pivot
+// columns are completed by the accumulated reflectors).  The decision is
+// taken on the device through a flag, so the sequence needs no host round trip
+// and can be captured in a CUDA graph:
+//   flag = 0  -> the CholeskyQR kernels run;
+//   flag = 1  -> breakdown seen; the Householder kernel runs and sets flag = 2;
+//   flag = 2  -> U is written; every later kernel of this QR returns at once.
+#include <algorithm>
+
+#include "internal.cuh"
+
+namespace hoqri {
+
+namespace {
+
+constexpr int GRAM_TPB = 256;
+constexpr int GRAM_ROWS = 32;   // rows staged per step
+constexpr int MAX_GRAM_BLOCKS = 304;
+constexpr int HH_TPB = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(GRAM_TPB) k_gram_partial(const T *A, int64_t I, int K, int64_t rows_per_block,
+                                                           double *part, const int32_t *flag) {
+    if (*flag != 0) return;
+    __shared__ double tile[GRAM_ROWS * HOQRI_MAXK];
+    const int npairs = K * (K + 1) / 2;
+    constexpr int MAXP = (HOQRI_MAXK * (HOQRI_MAXK + 1) / 2 + GRAM_TPB - 1) / GRAM_TPB;
+    double acc[MAXP];
+    int pi[MAXP], pj[MAXP];
+#pragma unroll
+    for (int q = 0; q < MAXP; ++q) {
+        acc[q] = 0.0;
+        int p = threadIdx.x + q * GRAM_TPB;
+        int i = 0, j = 0;
+        if (p < npairs) {
+            // pair p -> (i, j), i <= j, row-major over the upper triangle
+            int rem = p;
+            i = 0;
+            while (rem >= K - i) {
+                rem -= K - i;
+                ++i;
+            }
+            j = i + rem;
+        }
+        pi[q] = i;
+        pj[q] = j;
+    }
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(r0 + rows_per_block, I);
+    for (int64_t rb = r0; rb < r1; rb += GRAM_ROWS) {
+        const int nr = (int)min((int64_t)GRAM_ROWS, r1 - rb);
+        __syncthreads();
+        for (int t = threadIdx.x; t < nr * K; t += GRAM_TPB) tile[t] = (double)A[rb * K + t];
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < MAXP; ++q) {
+            if (threadIdx.x + q * GRAM_TPB < npairs) {
+                double s = acc[q];
+                for (int r = 0; r < nr; ++r) s += tile[r * K + pi[q]] * tile[r * K + pj[q]];
+                acc[q] = s;
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXP; ++q) {
+        int p = threadIdx.x + q * GRAM_TPB;
+        if (p < npairs) part[(size_t)blockIdx.x * npairs + p] = acc[q];
+    }
+}
+
+// Sum of the Gram partials in block order, Cholesky W = R^T R, Rinv = R^{-1}.
+// R overwrites the upper triangle of W in place (row j of R is formed from row
+// j of W and the rows of R above it).
+__global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int K, double *Rinv, int32_t *flag) {
+    if (*flag != 0) return;
+    __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
+    __shared__ int broke;
+    const int npairs = K * (K + 1) / 2;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        int rem = p, i = 0;
+        while (rem >= K - i) {
+            rem -= K - i;
+            ++i;
+        }
+        int j = i + rem;
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * npairs + p];
+        W[i * K + j] = s;
+    }
+    if (threadIdx.x == 0) broke = 0;
+    __syncthreads();
+    double dmax = 0.0;
+    for (int i = 0; i < K; ++i) dmax = fmax(dmax, W[i * K + i]);
+    const double tiny = 1e-14 * dmax;
+    for (int j = 0; j < K; ++j) {
+        if (threadIdx.x == 0) {
+            double d = W[j * K + j];
+            for (int i = 0; i < j; ++i) d -= W[i * K + j] * W[i * K + j];
+            if (!(d > tiny) || !(dmax > 0.0)) broke = 1;
+            W[j * K + j] = broke ? 1.0 : sqrt(d);
+        }
+        __syncthreads();
+        for (int k = j + 1 + threadIdx.x; k < K; k += blockDim.x) {
+            double s = W[j * K + k];
+            for (int i = 0; i < j; ++i) s -= W[i * K + j] * W[i * K + k];
+            W[j * K + k] = s / W[j * K + j];
+        }
+        __syncthreads();
+    }
+    if (broke) {
+        if (threadIdx.x == 0) {
+            *flag = 1;
+            flag[1] += 1;
+        }
+        return;
+    }
+    // Rinv: solve R X = I column by column (upper triangular)
+    for (int col = threadIdx.x; col < K; col += blockDim.x) {
+        for (int i = K - 1; i >= 0; --i) {
+            if (i > col) {
+                Rinv[i * K + col] = 0.0;
+                continue;
+            }
+            double s = (i == col) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= col; ++k) s -= W[i * K + k] * Rinv[k * K + col];
+            Rinv[i * K + col] = s / W[i * K + i];
+        }
+    }
+}
+
+// out(r, c) = sum_{i <= c} A(r, i) Rinv(i, c); one thread per output element (out != A)
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply(const T *A, int64_t I, int K, const double *Rinv, T *out,
+                                               const int32_t *flag) {
+    if (*flag != 0) return;
+    __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
+    __syncthreads();
+    const int64_t total = I * K;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / K;
+        const int c = (int)(t - r * K);
+        const T *a = A + r * K;
+        double s = 0.0;
+        for (int i = 0; i <= c; ++i) s += (double)a[i] * Rs[i * K + c];
+        out[t] = (T)s;
+    }
+}
+
+// in-place variant needs the whole row read before it is overwritten
+template <typename T>
+__global__ void __launch_bounds__(256) k_apply_inplace(T *A, int64_t I, int K, const double *Rinv, const int32_t *flag) {
+    if (*flag != 0) return;
+    __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
+    __syncthreads();
+    // one thread per row: reads the row into registers, then writes it
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
+        double a[HOQRI_MAXK];
+        for (int i = 0; i < K; ++i) a[i] = (double)A[r * K + i];
+        for (int c = 0; c < K; ++c) {
+            double s = 0.0;
+            for (int i = 0; i <= c; ++i) s += a[i] * Rs[i * K + c];
+            A[r * K + c] = (T)s;
+        }
+    }
+}
+
+__device__ double block_sum(double v, double *sh) {
+    // fixed-shape tree over HH_TPB threads
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = HH_TPB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// One-CTA Householder thin QR in FP64 (fallback).  W, Q: I x K doubles of workspace.
+template <typename T>
+__global__ void __launch_bounds__(HH_TPB) k_householder(const T *A, int64_t I, int K, double *W, double *Q, T *U,
+                                                        int32_t *flag) {
+    if (*flag != 1) return;
+    __shared__ double sh[HH_TPB];
+    __shared__ double beta[HOQRI_MAXK], diag[HOQRI_MAXK];
+    for (int64_t t = threadIdx.x; t < I * K; t += HH_TPB) W[t] = (double)A[t];
+    __syncthreads();
+    for (int j = 0; j < K; ++j) {
+        double s = 0.0;
+        for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) s += W[i * K + j] * W[i * K + j];
+        const double nrm = sqrt(block_sum(s, sh));
+        if (nrm == 0.0) {
+            if (threadIdx.x == 0) {
+                beta[j] = 0.0;
+                diag[j] = 0.0;
+            }
+            __syncthreads();
+            continue;
+        }
+        const double wjj = W[(int64_t)j * K + j];
+        const double alpha = wjj > 0 ? -nrm : nrm;
+        __syncthreads();
+        if (threadIdx.x == 0) W[(int64_t)j * K + j] = wjj - alpha;
+        __syncthreads();
+        s = 0.0;
+        for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) s += W[i * K + j] * W[i * K + j];
+        const double vn2 = block_sum(s, sh);
+        const double bj = vn2 > 0 ? 2.0 / vn2 : 0.0;
+        if (threadIdx.x == 0) {
+            beta[j] = bj;
+            diag[j] = alpha;
+        }
+        for (int c = j + 1; c < K; ++c) {
+            s = 0.0;
+            for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) s += W[i * K + j] * W[i * K + c];
+            const double f = bj * block_sum(s, sh);
+            for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) W[i * K + c] -= f * W[i * K + j];
+            __syncthreads();
+        }
+        __syncthreads();
+    }
+    // Q = H_0 ... H_{K-1} [I_K; 0]
+    for (int64_t t = threadIdx.x; t < I * K; t += HH_TPB) {
+        int64_t r = t / K;
+        int c = (int)(t - r * K);
+        Q[t] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int j = K - 1; j >= 0; --j) {
+        const double bj = beta[j];
+        if (bj == 0.0) continue;
+        for (int c = 0; c < K; ++c) {
+            double s = 0.0;
+            for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) s += W[i * K + j] * Q[i * K + c];
+            const double f = bj * block_sum(s, sh);
+            for (int64_t i = j + threadIdx.x; i < I; i += HH_TPB) Q[i * K + c] -= f * W[i * K + j];
+            __syncthreads();
+        }
+    }
+    for (int64_t t = threadIdx.x; t < I * K; t += HH_TPB) {
+        int c = (int)(t % K);
+        double v = Q[t];
+        U[t] = (T)(diag[c] < 0 ? -v : v);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *flag = 2;
+}
+
+// ---- seeded Gaussian initial factors: Philox4x32-10 (Salmon et al., SC'11) + Box-Muller
+
+__device__ __forceinline__ void philox_round(uint32_t c[4], uint32_t k[2]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    uint32_t hi0 = __umulhi(M0, c[0]), lo0 = M0 * c[0];
+    uint32_t hi1 = __umulhi(M1, c[2]), lo1 = M1 * c[2];
+    uint32_t n0 = hi1 ^ c[1] ^ k[0], n2 = hi0 ^ c[3] ^ k[1];
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+}
+
+__device__ void philox4x32_10(uint32_t ctr[4], uint64_t key64) {
+    uint32_t k[2] = {(uint32_t)key64, (uint32_t)(key64 >> 32)};
+    for (int r = 0; r < 10; ++r) {
+        philox_round(ctr, k);
+        k[0] += 0x9E3779B9u;
+        k[1] += 0xBB67AE85u;
+    }
+}
+
+template <typename T>
+__global__ void k_gauss(T *out, int64_t n, uint64_t seed, uint32_t stream_id) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t c[4] = {(uint32_t)t, (uint32_t)(t >> 32), stream_id, 0x484F5152u};
+        philox4x32_10(c, seed);
+        const double u1 = ((double)c[0] + 1.0) * (1.0 / 4294967296.0);  // (0, 1]
+        const double u2 = (double)c[1] * (1.0 / 4294967296.0);
+        out[t] = (T)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+}
+
+int gram_blocks(int64_t I) {
+    int64_t b = ceil_div(I, 256);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, MAX_GRAM_BLOCKS));
+}
+
+template <typename T>
+hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
+    const int64_t I = c->dims[n];
+    const int K = c->K[n];
+    cudaStream_t st = c->stream;
+    const int nb = gram_blocks(I);
+    const int64_t rpb = ceil_div(I, nb);
+    const int npairs = K * (K + 1) / 2;
+    double *Rinv = c->qr_small;
+    const int apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I * K, 256), (int64_t)c->num_sms * 8));
+    const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
+    if (c->opt.qr_kind == 1) {
+        int32_t one = 1;
+        HQ_CUDA(cudaMemcpyAsync(c->dflag, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    } else {
+        HQ_CUDA(cudaMemsetAsync(c->dflag, 0, sizeof(int32_t), st));
+    }
+    for (int pass = 0; pass < 2; ++pass) {
+        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(A, I, K, rpb, c->qr_part, c->dflag);
+        k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, Rinv, c->dflag);
+        k_householder<T><<<1, HH_TPB, 0, st>>>(A, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
+        if (pass == 0)
+            k_apply_inplace<T><<<apply_rows_grid, 256, 0, st>>>(A, I, K, Rinv, c->dflag);
+        else
+            k_apply<T><<<apply_grid, 256, 0, st>>>(A, I, K, Rinv, U, c->dflag);
+        c->nlaunch += 4;
+    }
+    (void)npairs;
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+}  // namespace
+
+hoqri_status qr_init(hoqri_ctx *c) {
+    int64_t maxIK = 0;
+    for (int n = 0; n < c->N; ++n) maxIK = std::max<int64_t>(maxIK, c->dims[n] * c->K[n]);
+    c->qr_part_bytes = (int64_t)MAX_GRAM_BLOCKS * (HOQRI_MAXK * (HOQRI_MAXK + 1) / 2) * sizeof(double);
+    HQ_TRY(dalloc(c, (void **)&c->qr_part, c->qr_part_bytes));
+    HQ_TRY(dalloc(c, (void **)&c->qr_small, HOQRI_MAXK * HOQRI_MAXK * sizeof(double)));
+    HQ_TRY(dalloc(c, (void **)&c->qr_work, 2 * maxIK * sizeof(double)));
+    return HOQRI_OK;
+}
+
+hoqri_status orthonormalize(hoqri_ctx *c, int n, void *A_inout, void *U_out) {
+    cudaEvent_t e0 = nullptr;
+    HQ_TRY(prof_begin(c, 2, &e0));
+    hoqri_status s = (c->prec == HOQRI_FP64) ? orthonormalize_t<double>(c, n, (double *)A_inout, (double *)U_out)
+                                             : orthonormalize_t<float>(c, n, (float *)A_inout, (float *)U_out);
+    HQ_TRY(s);
+    return prof_end(c, 2, e0);
+}
+
+hoqri_status init_factors_seeded(hoqri_ctx *c) {
+    for (int n = 0; n < c->N; ++n) {
+        const int64_t cnt = c->dims[n] * c->K[n];
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(cnt, 256), 4096));
+        if (c->prec == HOQRI_FP64)
+            k_gauss<double><<<g, 256, 0, c->stream>>>((double *)c->A, cnt, c->opt.seed, (uint32_t)n);
+        else
+            k_gauss<float><<<g, 256, 0, c->stream>>>((float *)c->A, cnt, c->opt.seed, (uint32_t)n);
+        c->nlaunch++;
+        HQ_TRY(orthonormalize(c, n, c->A, c->U[n]));
+    }
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+}  // namespace hoqri

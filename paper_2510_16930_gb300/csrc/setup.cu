@@ -1,0 +1,420 @@
+// Set-up of the sparse tensor on the device (once per tensor).
+//
+// 1. Check every index against its mode size.
+// 2. Sum repeated coordinates: stable radix sort of the coordinates into
+//    lexicographic (i_1, ..., i_N) order, then one FP64 sum per run in input
+//    order.  I(X) is a set of positions (Table 1), so repeats denote one entry.
+// 3. ||X||^2 in FP64.
+// 4. Per mode n: stable radix sort by i_n (ties keep the lexicographic order),
+//    the permutation perm_n, the other modes' indices and the values gathered
+//    into that order (structure of arrays), and the row descriptors: the
+//    non-empty mode-n slices I^(n)_{i_n} of Table 1 as (row_id, row_ptr).
+// 5. The partition of each sorted stream into warp tasks of C nonzeros.
+//
+// Sorting and compaction use CUB (CUDA's header library); everything here runs
+// once per tensor, outside the iteration.
+#include <cub/cub.cuh>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace hoqri {
+
+namespace {
+
+constexpr int TPB = 256;
+
+inline int grid_for(int64_t n, int tpb = TPB) {
+    int64_t g = (n + tpb - 1) / tpb;
+    return (int)std::min<int64_t>(std::max<int64_t>(g, 1), 1 << 30);
+}
+
+struct IdxPack {
+    const int32_t *p[HOQRI_MAXN];
+};
+struct IdxPackW {
+    int32_t *p[HOQRI_MAXN];
+};
+
+__global__ void k_validate(IdxPack idx, int N, int64_t nnz, const int64_t *dims_dev, int32_t *bad) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < nnz; z += (int64_t)gridDim.x * blockDim.x) {
+        for (int m = 0; m < N; ++m) {
+            int32_t v = idx.p[m][z];
+            if (v < 0 || (int64_t)v >= dims_dev[m]) atomicExch(bad, 1);
+        }
+    }
+}
+
+__global__ void k_pack_keys(IdxPack idx, int N, int64_t nnz, const int32_t *shift_dev, uint64_t *keys, int32_t *iota) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < nnz; z += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t k = 0;
+        for (int m = 0; m < N; ++m) k |= (uint64_t)(uint32_t)idx.p[m][z] << shift_dev[m];
+        keys[z] = k;
+        iota[z] = (int32_t)z;
+    }
+}
+
+__global__ void k_iota(int32_t *a, int64_t n) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < n; z += (int64_t)gridDim.x * blockDim.x)
+        a[z] = (int32_t)z;
+}
+
+__global__ void k_gather_key(const int32_t *src, const int32_t *perm, int64_t n, uint32_t *dst) {
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < n; z += (int64_t)gridDim.x * blockDim.x)
+        dst[z] = (uint32_t)src[perm[z]];
+}
+
+// head[s] = 1 if sorted position s starts a new coordinate
+__global__ void k_heads(IdxPack idx, int N, const int32_t *perm, int64_t n, int32_t *head) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        int h = 1;
+        if (s > 0) {
+            int32_t a = perm[s], b = perm[s - 1];
+            h = 0;
+            for (int m = 0; m < N; ++m) h |= (idx.p[m][a] != idx.p[m][b]);
+        }
+        head[s] = h;
+    }
+}
+
+__global__ void k_run_starts(const int32_t *head, const int32_t *incl, int64_t n, int64_t *run_start) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        if (head[s]) run_start[incl[s] - 1] = s;
+}
+
+template <typename T>
+__global__ void k_coalesce_values(IdxPack idx, IdxPackW cidx, int N, const int32_t *perm, const int64_t *run_start,
+                                  int64_t nu, int64_t n, const T *vals, T *cval) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = run_start[u], b = (u + 1 < nu) ? run_start[u + 1] : n;
+        double s = 0.0;
+        for (int64_t q = a; q < b; ++q) s += (double)vals[perm[q]];
+        cval[u] = (T)s;
+        int32_t z = perm[a];
+        for (int m = 0; m < N; ++m) cidx.p[m][u] = idx.p[m][z];
+    }
+}
+
+// deterministic FP64 sum of squares: fixed grid, fixed per-thread stride, tree in shared memory
+template <typename T>
+__global__ void k_sumsq_partial(const T *v, int64_t n, double *part) {
+    __shared__ double sh[TPB];
+    double s = 0.0;
+    for (int64_t z = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; z < n; z += (int64_t)gridDim.x * blockDim.x) {
+        double x = (double)v[z];
+        s += x * x;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = TPB / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_small(const double *part, int n, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += part[i];
+        *out = s;
+    }
+}
+
+template <typename T>
+__global__ void k_gather_mode(IdxPack cidx, IdxPackW oidx, int N, int n, const int32_t *perm, int64_t nnz,
+                              const T *cval, T *vals) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < nnz; s += (int64_t)gridDim.x * blockDim.x) {
+        int32_t u = perm[s];
+        int j = 0;
+        for (int m = 0; m < N; ++m) {
+            if (m == n) continue;
+            oidx.p[j++][s] = cidx.p[m][u];
+        }
+        vals[s] = cval[u];
+    }
+}
+
+__global__ void k_row_heads(const uint32_t *keys, int64_t n, int32_t *head) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        head[s] = (s == 0) || (keys[s] != keys[s - 1]);
+}
+
+__global__ void k_row_desc(const uint32_t *keys, const int32_t *head, const int32_t *incl, int64_t n, int32_t *row_id,
+                           int64_t *row_ptr) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x) {
+        if (head[s]) {
+            int32_t r = incl[s] - 1;
+            row_id[r] = (int32_t)keys[s];
+            row_ptr[r] = s;
+        }
+    }
+}
+
+__global__ void k_set_last(int64_t *row_ptr, int64_t R, int64_t n) { row_ptr[R] = n; }
+
+// chunk_row[c] = largest r with row_ptr[r] <= c*C
+__global__ void k_chunk_rows(const int64_t *row_ptr, int64_t R, int64_t nchunks, int32_t C, int32_t *chunk_row) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t pos = c * (int64_t)C;
+        int64_t lo = 0, hi = R - 1;
+        while (lo < hi) {
+            int64_t mid = (lo + hi + 1) >> 1;
+            if (row_ptr[mid] <= pos) lo = mid; else hi = mid - 1;
+        }
+        chunk_row[c] = (int32_t)lo;
+    }
+}
+
+__global__ void k_split_flags(const int64_t *row_ptr, int64_t R, int32_t C, char *flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = (row_ptr[r] / C) != ((row_ptr[r + 1] - 1) / C);
+}
+
+// RAII holder for set-up temporaries
+struct Tmp {
+    std::vector<void *> ptrs;
+    ~Tmp() {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    hoqri_status get(T **p, size_t count) {
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        if (e != cudaSuccess) {
+            set_error(std::string("set-up allocation: ") + cudaGetErrorString(e));
+            return HOQRI_ERR_OOM;
+        }
+        ptrs.push_back(q);
+        *p = (T *)q;
+        return HOQRI_OK;
+    }
+};
+
+int bits_for(int64_t dim) {
+    int b = 0;
+    while (b < 63 && ((int64_t)1 << b) < dim) ++b;
+    return std::max(b, 1);
+}
+
+}  // namespace
+
+template <typename T>
+static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw) {
+    cudaStream_t st = c->stream;
+    const int N = c->N;
+    Tmp tmp;
+    const int G = std::min(grid_for(nnz_raw), c->num_sms * 8);
+    IdxPack in{};
+    for (int m = 0; m < N; ++m) in.p[m] = idx_dev[m];
+
+    // ---- 1. validate
+    int64_t *dims_dev;
+    int32_t *bad;
+    HQ_TRY(tmp.get(&dims_dev, N));
+    HQ_TRY(tmp.get(&bad, 1));
+    HQ_CUDA(cudaMemcpyAsync(dims_dev, c->dims, N * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    HQ_CUDA(cudaMemsetAsync(bad, 0, sizeof(int32_t), st));
+    if (nnz_raw > 0) k_validate<<<G, TPB, 0, st>>>(in, N, nnz_raw, dims_dev, bad);
+    int32_t hbad = 0;
+    HQ_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HQ_CUDA(cudaStreamSynchronize(st));
+    if (hbad) {
+        set_error("hoqri_create: an index is outside [0, dims[m])");
+        return HOQRI_ERR_INVALID;
+    }
+
+    // ---- 2. lexicographic stable sort of the raw coordinates
+    int32_t *perm_a, *perm_b;
+    HQ_TRY(tmp.get(&perm_a, nnz_raw));
+    HQ_TRY(tmp.get(&perm_b, nnz_raw));
+    int32_t *perm = perm_a;
+    int total_bits = 0;
+    int32_t shift[HOQRI_MAXN];
+    for (int m = N - 1; m >= 0; --m) {
+        shift[m] = total_bits;
+        total_bits += bits_for(c->dims[m]);
+    }
+    const int nn = (int)nnz_raw;
+    if (nnz_raw > 0 && total_bits <= 64) {
+        uint64_t *ka, *kb;
+        int32_t *shift_dev;
+        HQ_TRY(tmp.get(&ka, nnz_raw));
+        HQ_TRY(tmp.get(&kb, nnz_raw));
+        HQ_TRY(tmp.get(&shift_dev, N));
+        HQ_CUDA(cudaMemcpyAsync(shift_dev, shift, N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_pack_keys<<<G, TPB, 0, st>>>(in, N, nnz_raw, shift_dev, ka, perm_a);
+        size_t tb = 0;
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, ka, kb, perm_a, perm_b, nn, 0, total_bits, st));
+        char *t;
+        HQ_TRY(tmp.get(&t, tb));
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(t, tb, ka, kb, perm_a, perm_b, nn, 0, total_bits, st));
+        perm = perm_b;
+    } else if (nnz_raw > 0) {
+        // least significant mode first; stable passes give lexicographic order
+        uint32_t *ka, *kb;
+        HQ_TRY(tmp.get(&ka, nnz_raw));
+        HQ_TRY(tmp.get(&kb, nnz_raw));
+        k_iota<<<G, TPB, 0, st>>>(perm_a, nnz_raw);
+        size_t tb = 0;
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, ka, kb, perm_a, perm_b, nn, 0, 32, st));
+        char *t;
+        HQ_TRY(tmp.get(&t, tb));
+        int32_t *src = perm_a, *dst = perm_b;
+        for (int m = N - 1; m >= 0; --m) {
+            k_gather_key<<<G, TPB, 0, st>>>(idx_dev[m], src, nnz_raw, ka);
+            HQ_CUDA(cub::DeviceRadixSort::SortPairs(t, tb, ka, kb, src, dst, nn, 0, bits_for(c->dims[m]), st));
+            std::swap(src, dst);
+        }
+        perm = src;
+    }
+
+    // ---- runs of equal coordinates
+    int32_t *head, *incl;
+    HQ_TRY(tmp.get(&head, nnz_raw));
+    HQ_TRY(tmp.get(&incl, nnz_raw));
+    int64_t nu = 0;
+    if (nnz_raw > 0) {
+        k_heads<<<G, TPB, 0, st>>>(in, N, perm, nnz_raw, head);
+        size_t tb = 0;
+        HQ_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, head, incl, nn, st));
+        char *t;
+        HQ_TRY(tmp.get(&t, tb));
+        HQ_CUDA(cub::DeviceScan::InclusiveSum(t, tb, head, incl, nn, st));
+        int32_t last = 0;
+        HQ_CUDA(cudaMemcpyAsync(&last, incl + nnz_raw - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        HQ_CUDA(cudaStreamSynchronize(st));
+        nu = last;
+    }
+    c->nnz = nu;
+
+    int64_t *run_start;
+    HQ_TRY(tmp.get(&run_start, nu));
+    IdxPackW cidx{};
+    for (int m = 0; m < N; ++m) HQ_TRY(tmp.get(&cidx.p[m], nu));
+    T *cval;
+    HQ_TRY(tmp.get(&cval, nu));
+    if (nu > 0) {
+        k_run_starts<<<G, TPB, 0, st>>>(head, incl, nnz_raw, run_start);
+        k_coalesce_values<T><<<std::min(grid_for(nu), c->num_sms * 8), TPB, 0, st>>>(
+            in, cidx, N, perm, run_start, nu, nnz_raw, (const T *)vals_dev, cval);
+    }
+
+    // ---- 3. ||X||^2
+    {
+        const int NB = 1024;
+        double *part;
+        HQ_TRY(tmp.get(&part, NB));
+        HQ_CUDA(cudaMemsetAsync(part, 0, NB * sizeof(double), st));
+        if (nu > 0) k_sumsq_partial<T><<<NB, TPB, 0, st>>>(cval, nu, part);
+        k_sum_small<<<1, 32, 0, st>>>(part, NB, c->dnorm + 0);
+    }
+
+    // ---- 4. per-mode sorted copies
+    IdxPack cin{};
+    for (int m = 0; m < N; ++m) cin.p[m] = cidx.p[m];
+    uint32_t *ka, *kb;
+    int32_t *ia;
+    HQ_TRY(tmp.get(&ka, nu));
+    HQ_TRY(tmp.get(&kb, nu));
+    HQ_TRY(tmp.get(&ia, nu));
+    int32_t *rhead, *rincl;
+    HQ_TRY(tmp.get(&rhead, nu));
+    HQ_TRY(tmp.get(&rincl, nu));
+    size_t tb_sort = 0, tb_scan = 0;
+    const int nun = (int)nu;
+    if (nu > 0) {
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb_sort, ka, kb, ia, ia, nun, 0, 32, st));
+        HQ_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb_scan, rhead, rincl, nun, st));
+    }
+    char *tsort, *tscan;
+    HQ_TRY(tmp.get(&tsort, tb_sort));
+    HQ_TRY(tmp.get(&tscan, tb_scan));
+    const int Gu = std::min(grid_for(nu), c->num_sms * 8);
+    for (int n = 0; n < N; ++n) {
+        ModeStore &M = c->ms[n];
+        HQ_TRY(dalloc(c, (void **)&M.perm, std::max<int64_t>(nu, 1) * sizeof(int32_t)));
+        HQ_TRY(dalloc(c, &M.vals, std::max<int64_t>(nu, 1) * sizeof(T)));
+        IdxPackW ow{};
+        for (int j = 0; j < N - 1; ++j) {
+            HQ_TRY(dalloc(c, (void **)&M.oidx[j], std::max<int64_t>(nu, 1) * sizeof(int32_t)));
+            ow.p[j] = M.oidx[j];
+        }
+        int64_t R = 0;
+        if (nu > 0) {
+            HQ_CUDA(cudaMemcpyAsync(ka, cidx.p[n], nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+            k_iota<<<Gu, TPB, 0, st>>>(ia, nu);
+            HQ_CUDA(cub::DeviceRadixSort::SortPairs(tsort, tb_sort, ka, kb, ia, M.perm, nun, 0, bits_for(c->dims[n]), st));
+            k_gather_mode<T><<<Gu, TPB, 0, st>>>(cin, ow, N, n, M.perm, nu, cval, (T *)M.vals);
+            k_row_heads<<<Gu, TPB, 0, st>>>(kb, nu, rhead);
+            HQ_CUDA(cub::DeviceScan::InclusiveSum(tscan, tb_scan, rhead, rincl, nun, st));
+            int32_t Rh = 0;
+            HQ_CUDA(cudaMemcpyAsync(&Rh, rincl + nu - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            HQ_CUDA(cudaStreamSynchronize(st));
+            R = Rh;
+        }
+        M.R = R;
+        HQ_TRY(dalloc(c, (void **)&M.row_id, std::max<int64_t>(R, 1) * sizeof(int32_t)));
+        HQ_TRY(dalloc(c, (void **)&M.row_ptr, (R + 1) * sizeof(int64_t)));
+        if (nu > 0) k_row_desc<<<Gu, TPB, 0, st>>>(kb, rhead, rincl, nu, M.row_id, M.row_ptr);
+        k_set_last<<<1, 1, 0, st>>>(M.row_ptr, R, nu);
+    }
+    HQ_CUDA(cudaGetLastError());
+    HQ_CUDA(cudaStreamSynchronize(st));
+    return HOQRI_OK;
+}
+
+hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw) {
+    if (nnz_raw >= (int64_t)INT32_MAX) {
+        set_error("hoqri_create: nnz must be below 2^31");
+        return HOQRI_ERR_UNSUPPORTED;
+    }
+    if (c->prec == HOQRI_FP64) return build_storage_t<double>(c, idx_dev, vals_dev, nnz_raw);
+    return build_storage_t<float>(c, idx_dev, vals_dev, nnz_raw);
+}
+
+hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C) {
+    ModeStore &M = c->ms[n];
+    cudaStream_t st = c->stream;
+    dfree(M.chunk_row);
+    dfree(M.split_row);
+    M.chunk_row = nullptr;
+    M.split_row = nullptr;
+    M.C = C;
+    M.nchunks = ceil_div(c->nnz, C);
+    M.nsplit = 0;
+    HQ_TRY(dalloc(c, (void **)&M.chunk_row, std::max<int64_t>(M.nchunks, 1) * sizeof(int32_t)));
+    if (M.nchunks == 0 || M.R == 0) {
+        HQ_TRY(dalloc(c, (void **)&M.split_row, sizeof(int32_t)));
+        return HOQRI_OK;
+    }
+    k_chunk_rows<<<grid_for(M.nchunks), TPB, 0, st>>>(M.row_ptr, M.R, M.nchunks, C, M.chunk_row);
+    Tmp tmp;
+    char *flag;
+    int32_t *sel, *it;
+    int *nsel;
+    HQ_TRY(tmp.get(&flag, M.R));
+    HQ_TRY(tmp.get(&sel, M.R));
+    HQ_TRY(tmp.get(&it, M.R));
+    HQ_TRY(tmp.get(&nsel, 1));
+    k_split_flags<<<grid_for(M.R), TPB, 0, st>>>(M.row_ptr, M.R, C, flag);
+    k_iota<<<grid_for(M.R), TPB, 0, st>>>(it, M.R);
+    size_t tb = 0;
+    HQ_CUDA(cub::DeviceSelect::Flagged(nullptr, tb, it, flag, sel, nsel, (int)M.R, st));
+    char *t;
+    HQ_TRY(tmp.get(&t, tb));
+    HQ_CUDA(cub::DeviceSelect::Flagged(t, tb, it, flag, sel, nsel, (int)M.R, st));
+    int hn = 0;
+    HQ_CUDA(cudaMemcpyAsync(&hn, nsel, sizeof(int), cudaMemcpyDeviceToHost, st));
+    HQ_CUDA(cudaStreamSynchronize(st));
+    M.nsplit = hn;
+    HQ_TRY(dalloc(c, (void **)&M.split_row, std::max<int64_t>(hn, 1) * sizeof(int32_t)));
+    if (hn > 0) HQ_CUDA(cudaMemcpyAsync(M.split_row, sel, hn * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    HQ_CUDA(cudaGetLastError());
+    HQ_CUDA(cudaStreamSynchronize(st));
+    return HOQRI_OK;
+}
+
+}  // namespace hoqri

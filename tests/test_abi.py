@@ -1,0 +1,54 @@
+"""The C-ABI library builds, loads and exports every symbol include/hoqri.h declares
+(no compute calls: these run without a GPU)."""
+import ctypes
+import os
+import re
+
+from paper_2510_16930_gb300 import build, hoqri
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hoqri.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hoqri_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_matches_binding():
+    assert _declared() == sorted(hoqri.SYMBOLS)
+
+
+def test_library_exports_all_symbols():
+    lib = ctypes.CDLL(str(build.build()))
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_default_options_and_error_text():
+    o = hoqri.hoqri_default_options()
+    assert o.prec == hoqri.HOQRI_FP32 and o.qr_kind == 0 and o.use_graphs == 1
+    assert ctypes.sizeof(hoqri.hoqri_options) == 40
+    assert isinstance(hoqri.hoqri_last_error(), str)
+
+
+def test_create_rejects_bad_arguments_without_gpu_work():
+    import numpy as np
+    # argument checks run before any device call: rank above the mode size
+    idx = [np.zeros(1, dtype=np.int32)] * 3
+    vals = np.ones(1, dtype=np.float32)
+    try:
+        hoqri.hoqri_create((2, 3, 4), (3, 2, 2), 1, idx, vals)
+        raise AssertionError("expected HOQRI_ERR_RANK")
+    except hoqri.HoqriError as e:
+        assert e.code == hoqri.HOQRI_ERR_RANK
+    try:  # order 1 is not a tensor decomposition
+        hoqri.hoqri_create((5,), (1,), 1, idx[:1], vals)
+        raise AssertionError("expected HOQRI_ERR_INVALID")
+    except hoqri.HoqriError as e:
+        assert e.code == hoqri.HOQRI_ERR_INVALID
+    try:  # K_n > prod_{m != n} K_m
+        hoqri.hoqri_create((9, 9, 9), (5, 2, 2), 1, idx, vals)
+        raise AssertionError("expected HOQRI_ERR_RANK")
+    except hoqri.HoqriError as e:
+        assert e.code == hoqri.HOQRI_ERR_RANK
