@@ -87,8 +87,9 @@ static void destroy_impl(hoqri_ctx *c) {
         dfree(M.perm);
         dfree(M.row_id);
         dfree(M.row_ptr);
+        dfree(M.chunk_start);
         dfree(M.chunk_row);
-        dfree(M.split_row);
+        dfree(M.big);
         dfree(c->U[n]);
     }
     dfree(c->G);
@@ -151,6 +152,17 @@ static hoqri_status prof_collect(hoqri_ctx *c) {
         c->ev_pool.push_back(r.b);
     }
     c->ev_recs.clear();
+    return HOQRI_OK;
+}
+
+// after a stream synchronisation: did a bounded device wait run out?
+static hoqri_status check_device_error(hoqri_ctx *c) {
+    int32_t e = 0;
+    HQ_CUDA(cudaMemcpy(&e, c->dflag + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (e) {
+        set_error("a bounded device wait ran out (staged copy never completed)");
+        return HOQRI_ERR_TIMEOUT;
+    }
     return HOQRI_OK;
 }
 
@@ -433,6 +445,7 @@ hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
         int32_t after = 0;
         HQ_CUDA(cudaMemcpyAsync(&after, c->dflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
         HQ_CUDA(cudaStreamSynchronize(c->stream));
+        HQ_TRY(check_device_error(c));
         if (resid_hist)
             for (int t = 0; t < iters; ++t) resid_hist[t] = resid_of(h[0], h[2 + (size_t)(t + 1) * N]);
         if (c->opt.qr_kind == 2 && after != before) {
@@ -513,7 +526,7 @@ hoqri_status hoqri_synchronize(hoqri_ctx *c) {
     HQ_TRY(check_mode(c, 0));
     HQ_CUDA(cudaStreamSynchronize(c->stream));
     HQ_CUDA(cudaGetLastError());
-    return HOQRI_OK;
+    return check_device_error(c);
 }
 
 }  // extern "C"

@@ -49,12 +49,15 @@ struct ModeStore {
     int64_t R = 0;                       // non-empty rows (slices)
     int32_t *row_id = nullptr;           // [R] mode-n index of each non-empty row
     int64_t *row_ptr = nullptr;          // [R+1] first sorted position of each row
-    // partition into warp tasks ("chunks") of C consecutive nonzeros
+    // Partition into warp tasks ("chunks") of at most C consecutive nonzeros:
+    // whole rows are packed together; a row longer than C is cut into pieces
+    // that are chunks of their own ("big" rows).
     int32_t C = 0;
     int64_t nchunks = 0;
-    int32_t *chunk_row = nullptr;        // [nchunks] row (index into row_id) holding the chunk start
-    int64_t nsplit = 0;
-    int32_t *split_row = nullptr;        // [nsplit] rows spanning more than one chunk
+    int64_t *chunk_start = nullptr;      // [nchunks+1] first sorted position of each chunk
+    int32_t *chunk_row = nullptr;        // [nchunks] first row (index into row_id) of each chunk
+    int64_t nbig = 0;
+    int32_t *big = nullptr;              // [3*nbig] (row, first chunk, last chunk) of each big row
 };
 
 struct Workspace;  // defined in the pass unit
@@ -81,7 +84,8 @@ struct hoqri_ctx {
     // [2 ...] ||G||^2 history of hoqri_iterate (one slot per core pass)
     double *dnorm = nullptr;
     int64_t dnorm_slots = 0;
-    int32_t *dflag = nullptr;           // [0] QR breakdown flag of the current QR, [1] breakdown count
+    int32_t *dflag = nullptr;           // [0] QR state of the current QR, [1] breakdown count,
+                                        // [2] device wait ran out (error)
     // scratch of the passes (partials); see passes.cu
     void *core_part = nullptr;          // per-CTA core partials
     int64_t core_part_bytes = 0;
@@ -94,6 +98,8 @@ struct hoqri_ctx {
     double *gnorm_part = nullptr;       // block partials of ||G||^2
     int core_grid = 0;                  // CTAs of the core pass (fixed per context)
     int pass_grid = 0;
+    int core_grid_fast = 0;             // the same for the register-tiled FP32 kernels
+    int pass_grid_fast = 0;
     int64_t device_bytes = 0;
     // CUDA graph of one sweep
     cudaGraphExec_t sweep_exec = nullptr;

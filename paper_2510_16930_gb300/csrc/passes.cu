@@ -10,14 +10,28 @@
 // This regroups the sums of Alg. 3 by row, which costs nnz*P_{-n} + R_n*P
 // multiply-adds, the second complexity of Table 2.
 //
-// Work split: the sorted stream is cut into chunks of C consecutive nonzeros,
-// one warp task each.  A row that crosses a chunk boundary is summed in pieces:
-// the core pass is linear in y_i, so pieces add into G directly; the TTMcTC pass
-// writes the piece's K_n-vector G_(n) y_piece to a per-chunk slot and a fix-up
-// kernel adds the pieces of each crossing row in chunk order.  No floating
-// point atomics anywhere: every sum has a fixed order for a given context, so
-// results are bitwise reproducible run to run.
+// Work split: the sorted stream is cut into chunks of at most C nonzeros, one
+// warp task each; whole rows are packed into a chunk, and a row longer than C
+// is cut into pieces that are chunks of their own.  The core pass is linear in
+// y_i, so pieces add into G directly; the TTMcTC pass writes each piece's
+// K_n-vector G_(n) y_piece to a per-chunk slot and a fix-up kernel adds the
+// pieces of each long row in chunk order.  No floating point atomics anywhere:
+// every sum has a fixed order for a given context, so results are bitwise
+// reproducible run to run.
+//
+// Two kernels implement the passes:
+//  - k_pass_fast (FP32): the y_i of a row is a sum of rank-1 terms z (x) v, with
+//    v the last other mode's factor row and z = x * (Kronecker product of the
+//    remaining ones).  Each lane owns a TL x TV register tile of y; the lanes
+//    of a warp form groups that take every NG-th nonzero of the row (split over
+//    nonzeros), and the group partial sums are added with warp shuffles at the
+//    row end.  The chunk's index and value streams are staged in shared memory
+//    by TMA bulk copies (cp.async.bulk, completion on an mbarrier), double
+//    buffered, so the next chunk is in flight while the current one computes.
+//  - k_pass_generic (any N <= 8, K <= 64, FP32 or FP64): y in registers, factor
+//    rows staged per nonzero in shared memory.
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -27,6 +41,67 @@ namespace {
 
 constexpr int GEN_WARPS = 4;  // warps per CTA of the generic pass kernel
 constexpr int RED_TPB = 256;
+constexpr size_t SMEM_CAP = 200 * 1024;
+constexpr int FAST_MAX_CTAS_PER_SM = 4;
+
+// ------------------------------------------------------------------ helpers
+
+template <typename T>
+__device__ __forceinline__ T shfl_idx(T v, int src) {
+    return __shfl_sync(0xffffffffu, v, src);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// bounded wait on an mbarrier phase; false (and *err set) if the limit ran out
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *err) {
+    const uint32_t a = smem_addr(bar);
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    if (err) atomicExch(err, 1);
+    return false;
+}
+
+// 1-D TMA bulk copy global -> shared, completion counted on an mbarrier.
+// dst, src and bytes are multiples of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ------------------------------------------------------------ generic kernel
 
 template <typename T>
 struct PassArgs {
@@ -44,36 +119,23 @@ struct PassArgs {
     const T *vals;
     const int64_t *row_ptr;
     const int32_t *row_id;
+    const int64_t *chunk_start;
     const int32_t *chunk_row;
     int64_t nchunks;
-    int64_t nnz;
-    int C;
     int wstride;                   // per-warp shared memory (elements of T)
     int acc_in_smem;               // core accumulator in shared memory (else global)
     T *acc_glob;                   // [grid*GEN_WARPS][Kn*Pm] when not in smem
     const T *Gn;                   // TTMcTC: G_(n) as [Kn][Pm]
     int gn_in_smem;
     T *A;                          // TTMcTC output, I_n x K_n
-    T *apart;                      // [nchunks][2][Kn]
+    T *apart;                      // [nchunks][Kn] pieces of long rows
     T *cpart;                      // core: [grid][Kn*Pm]
 };
 
-__device__ __forceinline__ float shfl_idx(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ double shfl_idx(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ int shfl_idx(int v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-
-template <typename T>
-__device__ __forceinline__ T warp_allsum(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Generic pass: any N <= 8, K <= 64, P_{-n} <= 32*PL.  y lives in registers
-// (element e = lane + 32*j of the lane); each nonzero's factor rows are staged
-// in the warp's shared row buffer, the Kronecker prefix z (all other modes but
-// the last) is formed once per nonzero in shared memory, and
-// y[e] += z[e / Kl] * u_last[e % Kl].
+// Generic pass: y lives in registers (element e = lane + 32*j of the lane);
+// each nonzero's factor rows are staged in the warp's shared row buffer, the
+// Kronecker prefix z (all other modes but the last) is formed once per nonzero
+// in shared memory, and y[e] += z[e / Kl] * u_last[e % Kl].
 template <typename T, int PL, bool CORE>
 __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -81,8 +143,7 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     const int KnPm = a.Kn * a.Pm;
-    // shared layout: [Gn (TTMcTC, optional)] [per-warp: rowbuf | zbuf | acc (core, optional)]
-    T *gn = a.Gn ? (T *)a.Gn : nullptr;
+    const T *gn = a.Gn;
     T *wbase = sm;
     if (!CORE && a.gn_in_smem) {
         for (int p = threadIdx.x; p < KnPm; p += blockDim.x) sm[p] = a.Gn[p];
@@ -93,8 +154,7 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     T *zbuf = rowbuf + a.rtot;
     T *acc = nullptr;
     if (CORE) {
-        acc = a.acc_in_smem ? zbuf + a.L
-                            : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + wib) * KnPm;
+        acc = a.acc_in_smem ? zbuf + a.L : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + wib) * KnPm;
         for (int p = lane; p < KnPm; p += 32) acc[p] = T(0);
     }
     __syncthreads();
@@ -111,10 +171,9 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     const int64_t nw = (int64_t)gridDim.x * GEN_WARPS;
 
     for (int64_t ch = gw; ch < a.nchunks; ch += nw) {
-        const int64_t s0 = ch * a.C;
-        const int64_t s1 = min(s0 + (int64_t)a.C, a.nnz);
-        const int32_t r_first = a.chunk_row[ch];
-        int32_t rr = r_first;
+        const int64_t s0 = a.chunk_start[ch];
+        const int64_t s1 = a.chunk_start[ch + 1];
+        int32_t rr = a.chunk_row[ch];
         int64_t pos = s0;
         while (pos < s1) {
             const int64_t rs = a.row_ptr[rr], re = a.row_ptr[rr + 1];
@@ -170,8 +229,7 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
                 }
             } else {
                 const bool full = (rs >= s0) && (re <= s1);
-                T *dst = full ? a.A + (int64_t)row * a.Kn
-                              : a.apart + (ch * 2 + (rr == r_first ? 0 : 1)) * a.Kn;
+                T *dst = full ? a.A + (int64_t)row * a.Kn : a.apart + ch * a.Kn;
                 for (int kn = 0; kn < a.Kn; ++kn) {
                     const T *g = gn + (size_t)kn * a.Pm;
                     T s = T(0);
@@ -203,22 +261,259 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     }
 }
 
-// sum of the per-chunk pieces of each row that crosses chunk boundaries
-template <typename T>
-__global__ void k_fixup(const int32_t *split_row, int64_t nsplit, const int64_t *row_ptr, const int32_t *row_id,
-                        const int32_t *chunk_row, int C, const T *apart, int Kn, T *A) {
+// --------------------------------------------------------------- fast kernel
+
+struct FastArgs {
+    int Kn, Pm, Kl;                // K_n, P_{-n}, rank of the last other mode
+    int Ka, Kb;                    // row strides of Ua / Ub
+    int GL, GV, lpn;               // lane grid of one nonzero group: GL x GV lanes, lpn = GL*GV
+    const int32_t *ia, *ib, *ic;   // other-mode index streams (ascending m != n)
+    const float *Ua, *Ub, *Uc;
+    const float *Un;
+    const float *vals;
+    const int64_t *row_ptr;
+    const int32_t *row_id;
+    const int64_t *chunk_start;
+    const int32_t *chunk_row;
+    int64_t nchunks;
+    int Cbuf;                      // elements per staged array (C + 4)
+    int warps;                     // warps per CTA
+    int gs_off, w_off, w_stride;   // shared memory layout (floats): Gs, first warp, per-warp stride
+    const float *Gn;               // [Kn][Pm]
+    float *A;
+    float *apart;
+    float *cpart;                  // [grid][Kn*Pm]
+    int32_t *err;
+};
+
+template <int TN>
+__device__ __forceinline__ void ldg_vec(float (&d)[TN], const float *p) {
+#pragma unroll
+    for (int q = 0; q < TN / 4; ++q) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
+        d[4 * q + 0] = t.x;
+        d[4 * q + 1] = t.y;
+        d[4 * q + 2] = t.z;
+        d[4 * q + 3] = t.w;
+    }
+}
+
+// NM1 = N - 1 in {2, 3}.  For NM1 = 2, y = sum (x u_a) (x) u_b: z-rows from Ua,
+// v-rows from Ub.  For NM1 = 3, y = sum (x u_a(ka) u_b) (x) u_c over the tile's
+// single ka: scalar from Ua, z-rows from Ub, v-rows from Uc.
+template <int NM1, int TL, int TV, bool CORE>
+__global__ void __launch_bounds__(256) k_pass_fast(FastArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *smf = reinterpret_cast<float *>(smem_raw);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);  // 2 per warp, at the start
     const int lane = threadIdx.x & 31;
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (w >= nsplit) return;
-    const int32_t r = split_row[w];
-    const int64_t c0 = row_ptr[r] / C, c1 = (row_ptr[r + 1] - 1) / C;
-    const int first_slot = (chunk_row[c0] == r) ? 0 : 1;
+    const int w = threadIdx.x >> 5;
+    const int lpn = a.lpn;
+    const int NG = 32 / lpn;
+    const int g = lane / lpn;
+    const int sub = lane - g * lpn;
+    const int gl = sub / a.GV;
+    const int gv = sub - gl * a.GV;
+    const int l0 = gl * TL;  // first y row of the lane's tile
+    const int v0 = gv * TV;  // first y column
+    int ka = 0, kb0 = l0;
+    if (NM1 == 3) {
+        ka = l0 / a.Kb;
+        kb0 = l0 - ka * a.Kb;
+    }
+    const int KnPm = a.Kn * a.Pm;
+    const float *Gs = smf + a.gs_off;
+    float *wbase = smf + a.w_off + (size_t)w * a.w_stride;
+    constexpr int NARR = NM1 + 1;
+    float *acc = wbase + 2 * NARR * a.Cbuf;  // core accumulator [Kn][Pm] (CORE only)
+    uint64_t *bar = bars + 2 * w;
+
+    if (threadIdx.x == 0)
+        for (int q = 0; q < 2 * a.warps; ++q) mbar_init(bars + q, 1);
+    if (!CORE)
+        for (int p = threadIdx.x; p < KnPm; p += blockDim.x) smf[a.gs_off + p] = a.Gn[p];
+    if (CORE)
+        for (int p = lane; p < KnPm; p += 32) acc[p] = 0.f;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncthreads();
+
+    const int64_t gw = (int64_t)blockIdx.x * a.warps + w;
+    const int64_t nw = (int64_t)gridDim.x * a.warps;
+
+    auto issue = [&](int64_t ch, int buf) {
+        if (lane == 0) {
+            const int64_t s0 = a.chunk_start[ch], s1 = a.chunk_start[ch + 1];
+            const int64_t al = s0 & ~(int64_t)3;
+            const uint32_t n4 = (uint32_t)(((s1 - al) + 3) & ~(int64_t)3);
+            const uint32_t bytes = n4 * 4u;
+            float *dst = wbase + (size_t)buf * NARR * a.Cbuf;
+            fence_proxy_async();
+            mbar_expect_tx(bar + buf, bytes * NARR);
+            bulk_g2s(dst, a.ia + al, bytes, bar + buf);
+            bulk_g2s(dst + a.Cbuf, a.ib + al, bytes, bar + buf);
+            if (NM1 == 3) bulk_g2s(dst + 2 * a.Cbuf, a.ic + al, bytes, bar + buf);
+            bulk_g2s(dst + (NARR - 1) * a.Cbuf, a.vals + al, bytes, bar + buf);
+        }
+    };
+
+    bool ok = true;
+    int it = 0;
+    if (gw < a.nchunks) issue(gw, 0);
+    for (int64_t ch = gw; ch < a.nchunks; ch += nw, ++it) {
+        const int buf = it & 1;
+        if (ch + nw < a.nchunks) issue(ch + nw, buf ^ 1);
+        if (!mbar_wait(bar + buf, (uint32_t)((it >> 1) & 1), a.err)) {
+            ok = false;
+            break;
+        }
+        const int64_t s0 = a.chunk_start[ch], s1 = a.chunk_start[ch + 1];
+        const int off = (int)(s0 & 3);
+        const float *mb = wbase + (size_t)buf * NARR * a.Cbuf;
+        const int32_t *mia = reinterpret_cast<const int32_t *>(mb) + off;
+        const int32_t *mib = reinterpret_cast<const int32_t *>(mb + a.Cbuf) + off;
+        const int32_t *mic = reinterpret_cast<const int32_t *>(mb + 2 * a.Cbuf) + off;
+        const float *mval = mb + (NARR - 1) * a.Cbuf + off;
+
+        auto load_nz = [&](int q, float (&z)[TL], float (&v)[TV]) {
+            const float x = mval[q];
+            if (NM1 == 2) {
+                ldg_vec<TL>(z, a.Ua + (int64_t)mia[q] * a.Ka + l0);
+                ldg_vec<TV>(v, a.Ub + (int64_t)mib[q] * a.Kl + v0);
+#pragma unroll
+                for (int j = 0; j < TL; ++j) z[j] *= x;
+            } else {
+                const float s = x * __ldg(a.Ua + (int64_t)mia[q] * a.Ka + ka);
+                ldg_vec<TL>(z, a.Ub + (int64_t)mib[q] * a.Kb + kb0);
+                ldg_vec<TV>(v, a.Uc + (int64_t)mic[q] * a.Kl + v0);
+#pragma unroll
+                for (int j = 0; j < TL; ++j) z[j] *= s;
+            }
+        };
+
+        int32_t rr = a.chunk_row[ch];
+        int64_t pos = s0;
+        while (pos < s1) {
+            const int64_t rs = a.row_ptr[rr], re = a.row_ptr[rr + 1];
+            const int64_t a1 = min(re, s1);
+            if (a1 <= pos) break;  // row descriptors always advance; never spin on bad input
+            float y[TL][TV];
+#pragma unroll
+            for (int j = 0; j < TL; ++j)
+#pragma unroll
+                for (int k = 0; k < TV; ++k) y[j][k] = 0.f;
+            const int qe = (int)(a1 - s0);
+            int q = (int)(pos - s0) + g;
+            float z0[TL], w0[TV], z1[TL], w1[TV];
+            if (q < qe) load_nz(q, z0, w0);
+            while (q < qe) {
+                int qn = q + NG;
+                if (qn < qe) load_nz(qn, z1, w1);
+#pragma unroll
+                for (int j = 0; j < TL; ++j)
+#pragma unroll
+                    for (int k = 0; k < TV; ++k) y[j][k] = fmaf(z0[j], w0[k], y[j][k]);
+                q = qn;
+                if (q >= qe) break;
+                qn = q + NG;
+                if (qn < qe) load_nz(qn, z0, w0);
+#pragma unroll
+                for (int j = 0; j < TL; ++j)
+#pragma unroll
+                    for (int k = 0; k < TV; ++k) y[j][k] = fmaf(z1[j], w1[k], y[j][k]);
+                q = qn;
+            }
+            __syncwarp();
+            // sum the groups' partial y (every lane then holds its tile of the full y_i)
+            for (int o = lpn; o < 32; o <<= 1) {
+#pragma unroll
+                for (int j = 0; j < TL; ++j)
+#pragma unroll
+                    for (int k = 0; k < TV; ++k) y[j][k] += __shfl_xor_sync(0xffffffffu, y[j][k], o);
+            }
+            const int32_t row = a.row_id[rr];
+            if (CORE) {
+                // acc[kn][e] += U_n(row, kn) * y[e]; group g owns kn = g, g + NG, ...
+                for (int kn = g; kn < a.Kn; kn += NG) {
+                    const float u = __ldg(a.Un + (int64_t)row * a.Kn + kn);
+#pragma unroll
+                    for (int j = 0; j < TL; ++j) {
+                        float4 *ap = reinterpret_cast<float4 *>(acc + (size_t)kn * a.Pm + (size_t)(l0 + j) * a.Kl + v0);
+#pragma unroll
+                        for (int k4 = 0; k4 < TV / 4; ++k4) {
+                            float4 t = ap[k4];
+                            t.x = fmaf(u, y[j][4 * k4 + 0], t.x);
+                            t.y = fmaf(u, y[j][4 * k4 + 1], t.y);
+                            t.z = fmaf(u, y[j][4 * k4 + 2], t.z);
+                            t.w = fmaf(u, y[j][4 * k4 + 3], t.w);
+                            ap[k4] = t;
+                        }
+                    }
+                }
+            } else {
+                const bool full = (rs >= s0) && (re <= s1);
+                float *dst = full ? a.A + (int64_t)row * a.Kn : a.apart + ch * a.Kn;
+                const int rounds = (a.Kn + NG - 1) / NG;
+                for (int t = 0; t < rounds; ++t) {
+                    const int kn = t * NG + g;
+                    float s = 0.f;
+                    if (kn < a.Kn) {
+#pragma unroll
+                        for (int j = 0; j < TL; ++j) {
+                            const float4 *gp =
+                                reinterpret_cast<const float4 *>(Gs + (size_t)kn * a.Pm + (size_t)(l0 + j) * a.Kl + v0);
+#pragma unroll
+                            for (int k4 = 0; k4 < TV / 4; ++k4) {
+                                const float4 gq = gp[k4];
+                                s = fmaf(gq.x, y[j][4 * k4 + 0], s);
+                                s = fmaf(gq.y, y[j][4 * k4 + 1], s);
+                                s = fmaf(gq.z, y[j][4 * k4 + 2], s);
+                                s = fmaf(gq.w, y[j][4 * k4 + 3], s);
+                            }
+                        }
+                    }
+                    for (int o = 1; o < lpn; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+                    if (sub == 0 && kn < a.Kn) dst[kn] = s;
+                }
+            }
+            pos = a1;
+            ++rr;
+        }
+        __syncwarp();
+    }
+    if (!ok) {
+        // a staged copy never completed: wait (bounded) for the other buffer, then leave
+        mbar_wait(bar + ((it + 1) & 1), (uint32_t)(((it + 1) >> 1) & 1), nullptr);
+    }
+    if (CORE) {
+        __syncthreads();
+        for (int p = threadIdx.x; p < KnPm; p += blockDim.x) {
+            float s = 0.f;
+            for (int q = 0; q < a.warps; ++q) s += smf[a.w_off + (size_t)q * a.w_stride + 2 * NARR * a.Cbuf + p];
+            a.cpart[(size_t)blockIdx.x * KnPm + p] = s;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ fix-up
+
+// A(row, :) of every row longer than C = sum of its pieces' slots, in chunk order.
+template <typename T>
+__global__ void __launch_bounds__(128) k_fixup(const int32_t *big, const int32_t *row_id, const T *apart, int Kn,
+                                               T *A) {
+    __shared__ double sh[128];
+    const int b = blockIdx.x;
+    const int32_t r = big[3 * b], c0 = big[3 * b + 1], c1 = big[3 * b + 2];
     for (int kn = 0; kn < Kn; ++kn) {
         double s = 0.0;
-        for (int64_t c = c0 + lane; c <= c1; c += 32)
-            s += (double)apart[(c * 2 + (c == c0 ? first_slot : 0)) * Kn + kn];
-        s = warp_allsum(s);
-        if (lane == 0) A[(int64_t)row_id[r] * Kn + kn] = (T)s;
+        for (int c = c0 + (int)threadIdx.x; c <= c1; c += blockDim.x) s += (double)apart[(int64_t)c * Kn + kn];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = 64; o > 0; o >>= 1) {
+            if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) A[(int64_t)row_id[r] * Kn + kn] = (T)sh[0];
+        __syncthreads();
     }
 }
 
@@ -280,35 +575,7 @@ __global__ void k_core_to_unfolded(const T *G, CoreMap m, T *Gn) {
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) Gn[p] = G[rowmajor_of(m, p)];
 }
 
-template <typename T>
-void fill_common(hoqri_ctx *c, int n, PassArgs<T> &a) {
-    const ModeStore &M = c->ms[n];
-    a.nm1 = c->N - 1;
-    a.Kn = c->K[n];
-    int j = 0, off = 0;
-    a.Pm = 1;
-    for (int m = 0; m < c->N; ++m) {
-        if (m == n) continue;
-        a.Ko[j] = c->K[m];
-        a.roff[j] = off;
-        off += c->K[m];
-        a.Pm *= c->K[m];
-        a.oidx[j] = M.oidx[j];
-        a.Uo[j] = (const T *)c->U[m];
-        ++j;
-    }
-    a.rtot = off;
-    a.Kl = a.Ko[a.nm1 - 1];
-    a.L = a.Pm / a.Kl;
-    a.Un = (const T *)c->U[n];
-    a.vals = (const T *)M.vals;
-    a.row_ptr = M.row_ptr;
-    a.row_id = M.row_id;
-    a.chunk_row = M.chunk_row;
-    a.nchunks = M.nchunks;
-    a.nnz = c->nnz;
-    a.C = M.C;
-}
+// ------------------------------------------------------------ host side
 
 CoreMap core_map(hoqri_ctx *c, int n) {
     CoreMap m{};
@@ -334,6 +601,76 @@ int pl_for(int Pm) {
     int pl = 1;
     while (32 * pl < Pm) pl <<= 1;
     return pl;
+}
+
+// ---- fast-path plan for mode n
+
+struct FastPlan {
+    bool ok = false;
+    int nm1 = 0, TL = 0, TV = 0, GL = 0, GV = 0, lpn = 0;
+    int Ka = 0, Kb = 0, Kl = 0, Pm = 0;
+};
+
+bool pow2_ge4(int k) { return k >= 4 && k <= 64 && (k & (k - 1)) == 0; }
+
+FastPlan fast_plan(const hoqri_ctx *c, int n) {
+    FastPlan p;
+    if (c->prec != HOQRI_FP32 || (c->N != 3 && c->N != 4)) return p;
+    int Ko[3], j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) Ko[j++] = c->K[m];
+    for (int q = 0; q < j; ++q)
+        if (!pow2_ge4(Ko[q])) return p;
+    p.nm1 = c->N - 1;
+    p.Kl = Ko[p.nm1 - 1];
+    p.TV = std::min(8, p.Kl);
+    p.GV = p.Kl / p.TV;
+    int L;
+    if (p.nm1 == 2) {
+        p.Ka = Ko[0];
+        L = Ko[0];
+        p.TL = std::min(8, L);
+    } else {
+        p.Ka = Ko[0];
+        p.Kb = Ko[1];
+        L = Ko[0] * Ko[1];
+        p.TL = std::min(8, Ko[1]);
+    }
+    p.GL = L / p.TL;
+    p.lpn = p.GL * p.GV;
+    p.Pm = L * p.Kl;
+    if (p.lpn > 32) return p;
+    p.ok = true;
+    return p;
+}
+
+template <typename T>
+void fill_common(hoqri_ctx *c, int n, PassArgs<T> &a) {
+    const ModeStore &M = c->ms[n];
+    a.nm1 = c->N - 1;
+    a.Kn = c->K[n];
+    int j = 0, off = 0;
+    a.Pm = 1;
+    for (int m = 0; m < c->N; ++m) {
+        if (m == n) continue;
+        a.Ko[j] = c->K[m];
+        a.roff[j] = off;
+        off += c->K[m];
+        a.Pm *= c->K[m];
+        a.oidx[j] = M.oidx[j];
+        a.Uo[j] = (const T *)c->U[m];
+        ++j;
+    }
+    a.rtot = off;
+    a.Kl = a.Ko[a.nm1 - 1];
+    a.L = a.Pm / a.Kl;
+    a.Un = (const T *)c->U[n];
+    a.vals = (const T *)M.vals;
+    a.row_ptr = M.row_ptr;
+    a.row_id = M.row_id;
+    a.chunk_start = M.chunk_start;
+    a.chunk_row = M.chunk_row;
+    a.nchunks = M.nchunks;
 }
 
 template <typename T, bool CORE>
@@ -364,28 +701,135 @@ hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem)
     return HOQRI_OK;
 }
 
-constexpr size_t SMEM_CAP = 200 * 1024;
+// fast kernel configuration: warps per CTA and shared memory bytes
+struct FastLaunch {
+    int warps = 0;
+    size_t smem = 0;
+    int gs_off = 0, w_off = 0, w_stride = 0;
+};
+
+FastLaunch fast_launch(const hoqri_ctx *c, int n, const FastPlan &p, bool core) {
+    FastLaunch L;
+    const int Kn = c->K[n];
+    const int KnPm = Kn * p.Pm;
+    const int Cbuf = c->ms[n].C + 4;
+    const int narr = p.nm1 + 1;
+    L.warps = core ? 4 : 8;
+    // floats: [mbarriers: 2 per warp, padded to 32 floats] [Gs (TTMcTC)] [per warp: 2 x narr x Cbuf (+ acc)]
+    L.gs_off = 32;
+    int gs = core ? 0 : ((KnPm + 31) & ~31);
+    L.w_off = L.gs_off + gs;
+    L.w_stride = ((2 * narr * Cbuf + (core ? KnPm : 0)) + 31) & ~31;
+    L.smem = (size_t)(L.w_off + L.warps * L.w_stride) * sizeof(float);
+    return L;
+}
+
+// Grid = resident CTAs (SMs x CTAs per SM from the occupancy calculator),
+// capped by the number of warp tasks; it depends only on the device, kernel
+// and shape, so a context always uses the same grid (fixed summation order).
+template <int NM1, bool CORE>
+hoqri_status launch_fast_nm1(hoqri_ctx *c, const FastPlan &p, FastArgs &a, const FastLaunch &L, int *grid) {
+#define HQ_FAST(TLV, TVV)                                                                                  \
+    if (p.TL == TLV && p.TV == TVV) {                                                                      \
+        auto kern = k_pass_fast<NM1, TLV, TVV, CORE>;                                                      \
+        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));    \
+        int per_sm = 0;                                                                                    \
+        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.warps * 32, L.smem));      \
+        per_sm = std::max(1, std::min(per_sm, FAST_MAX_CTAS_PER_SM));                                      \
+        *grid = (int)std::max<int64_t>(                                                                    \
+            1, std::min<int64_t>((int64_t)c->num_sms * per_sm, ceil_div(std::max<int64_t>(a.nchunks, 1), L.warps))); \
+        kern<<<*grid, L.warps * 32, L.smem, c->stream>>>(a);                                               \
+        c->nlaunch++;                                                                                      \
+        HQ_CUDA(cudaGetLastError());                                                                       \
+        return HOQRI_OK;                                                                                   \
+    }
+    HQ_FAST(8, 8)
+    HQ_FAST(8, 4)
+    HQ_FAST(4, 8)
+    HQ_FAST(4, 4)
+#undef HQ_FAST
+    set_error("fast pass: no kernel for this tile");
+    return HOQRI_ERR_UNSUPPORTED;
+}
+
+template <bool CORE>
+hoqri_status launch_fast(hoqri_ctx *c, int n, const FastPlan &p, const float *Gn, float *A_out, int *grid) {
+    const ModeStore &M = c->ms[n];
+    FastArgs a{};
+    a.Kn = c->K[n];
+    a.Pm = p.Pm;
+    a.Kl = p.Kl;
+    a.Ka = p.Ka;
+    a.Kb = p.Kb;
+    a.GL = p.GL;
+    a.GV = p.GV;
+    a.lpn = p.lpn;
+    const float *Uo[3] = {nullptr, nullptr, nullptr};
+    int j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) Uo[j++] = (const float *)c->U[m];
+    a.ia = M.oidx[0];
+    a.ib = M.oidx[1];
+    a.ic = p.nm1 == 3 ? M.oidx[2] : nullptr;
+    a.Ua = Uo[0];
+    a.Ub = Uo[1];
+    a.Uc = Uo[2];
+    a.Un = (const float *)c->U[n];
+    a.vals = (const float *)M.vals;
+    a.row_ptr = M.row_ptr;
+    a.row_id = M.row_id;
+    a.chunk_start = M.chunk_start;
+    a.chunk_row = M.chunk_row;
+    a.nchunks = M.nchunks;
+    a.Cbuf = M.C + 4;
+    FastLaunch L = fast_launch(c, n, p, CORE);
+    a.warps = L.warps;
+    a.gs_off = L.gs_off;
+    a.w_off = L.w_off;
+    a.w_stride = L.w_stride;
+    a.Gn = Gn;
+    a.A = A_out;
+    a.apart = (float *)c->a_part;
+    a.cpart = (float *)c->core_part;
+    a.err = c->dflag + 2;
+    if (p.nm1 == 2) return launch_fast_nm1<2, CORE>(c, p, a, L, grid);
+    return launch_fast_nm1<3, CORE>(c, p, a, L, grid);
+}
+
+bool use_fast(const hoqri_ctx *c, int n, bool core, FastPlan *out) {
+    FastPlan p = fast_plan(c, n);
+    if (!p.ok || c->ms[n].C % 4 != 0) return false;
+    FastLaunch L = fast_launch(c, n, p, core);
+    if (L.smem > SMEM_CAP) return false;
+    *out = p;
+    return true;
+}
 
 template <typename T>
 hoqri_status core_pass_t(hoqri_ctx *c, int n, void *G_out, double *normG2_slot) {
     PassArgs<T> a{};
     fill_common<T>(c, n, a);
     const int KnPm = a.Kn * a.Pm;
-    a.wstride = (a.rtot + a.L + KnPm + 3) & ~3;
-    size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
-    a.acc_in_smem = smem <= SMEM_CAP;
-    if (!a.acc_in_smem) {
-        a.wstride = (a.rtot + a.L + 3) & ~3;
-        smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
+    int grid = c->core_grid;
+    FastPlan fp;
+    if (std::is_same<T, float>::value && use_fast(c, n, true, &fp)) {
+        HQ_TRY(launch_fast<true>(c, n, fp, nullptr, nullptr, &grid));
+    } else {
+        a.wstride = (a.rtot + a.L + KnPm + 3) & ~3;
+        size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
+        a.acc_in_smem = smem <= SMEM_CAP;
+        if (!a.acc_in_smem) {
+            a.wstride = (a.rtot + a.L + 3) & ~3;
+            smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
+        }
+        a.acc_glob = (T *)c->a_part;  // only used when the accumulator does not fit in smem
+        a.cpart = (T *)c->core_part;
+        if (!a.acc_in_smem && (int64_t)grid * GEN_WARPS * KnPm * (int64_t)sizeof(T) > c->a_part_bytes) {
+            set_error("core pass: accumulator workspace too small");
+            return HOQRI_ERR_UNSUPPORTED;
+        }
+        HQ_TRY((launch_generic<T, true>(c, a, grid, smem)));
     }
-    const int grid = c->core_grid;
-    a.acc_glob = (T *)c->a_part;  // only used when the accumulator does not fit in smem
-    a.cpart = (T *)c->core_part;
-    if (!a.acc_in_smem && (int64_t)grid * GEN_WARPS * KnPm * (int64_t)sizeof(T) > c->a_part_bytes) {
-        set_error("core pass: accumulator workspace too small");
-        return HOQRI_ERR_UNSUPPORTED;
-    }
-    HQ_TRY((launch_generic<T, true>(c, a, grid, smem)));
     CoreMap m = core_map(c, n);
     const int rb = std::max(1, std::min(64, (KnPm + RED_TPB - 1) / RED_TPB));
     k_core_reduce<T><<<rb, RED_TPB, 0, c->stream>>>((const T *)c->core_part, grid, m, (T *)G_out, c->gnorm_part);
@@ -406,24 +850,26 @@ hoqri_status ttmctc_pass_t(hoqri_ctx *c, int n, const void *G, void *A_out) {
     k_core_to_unfolded<T><<<std::max(1, std::min(64, (KnPm + 255) / 256)), 256, 0, c->stream>>>((const T *)G, m, Gn);
     c->nlaunch++;
     HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * a.Kn * sizeof(T), c->stream));
-    a.Gn = Gn;
-    a.A = (T *)A_out;
-    a.apart = (T *)c->a_part;
-    if ((int64_t)M.nchunks * 2 * a.Kn * (int64_t)sizeof(T) > c->a_part_bytes) {
+    if ((int64_t)M.nchunks * a.Kn * (int64_t)sizeof(T) > c->a_part_bytes) {
         set_error("TTMcTC pass: partial-row workspace too small");
         return HOQRI_ERR_UNSUPPORTED;
     }
-    a.wstride = (a.rtot + a.L + 3) & ~3;
-    size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
-    a.gn_in_smem = (smem + (size_t)KnPm * sizeof(T)) <= SMEM_CAP;
-    if (a.gn_in_smem) smem += (size_t)KnPm * sizeof(T);
-    const int grid = c->pass_grid;
-    HQ_TRY((launch_generic<T, false>(c, a, grid, smem)));
-    if (M.nsplit > 0) {
-        const int tpb = 256;
-        const int64_t blocks = ceil_div(M.nsplit * 32, tpb);
-        k_fixup<T><<<(unsigned)blocks, tpb, 0, c->stream>>>(M.split_row, M.nsplit, M.row_ptr, M.row_id, M.chunk_row,
-                                                            M.C, (const T *)c->a_part, a.Kn, (T *)A_out);
+    FastPlan fp;
+    if (std::is_same<T, float>::value && use_fast(c, n, false, &fp)) {
+        int grid = 0;
+        HQ_TRY(launch_fast<false>(c, n, fp, (const float *)Gn, (float *)A_out, &grid));
+    } else {
+        a.Gn = Gn;
+        a.A = (T *)A_out;
+        a.apart = (T *)c->a_part;
+        a.wstride = (a.rtot + a.L + 3) & ~3;
+        size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
+        a.gn_in_smem = (smem + (size_t)KnPm * sizeof(T)) <= SMEM_CAP;
+        if (a.gn_in_smem) smem += (size_t)KnPm * sizeof(T);
+        HQ_TRY((launch_generic<T, false>(c, a, c->pass_grid, smem)));
+    }
+    if (M.nbig > 0) {
+        k_fixup<T><<<(unsigned)M.nbig, 128, 0, c->stream>>>(M.big, M.row_id, (const T *)c->a_part, a.Kn, (T *)A_out);
         c->nlaunch++;
     }
     HQ_CUDA(cudaGetLastError());
@@ -438,11 +884,12 @@ int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 hoqri_status passes_init(hoqri_ctx *c) {
     int32_t C = c->opt.chunk_nnz;
     if (C <= 0) {
-        // about 8 tasks per resident warp, within [32, 2048]
+        // about 8 tasks per resident warp, within [32, 256]
         int64_t target = ceil_div(c->nnz, (int64_t)c->num_sms * 16 * 8);
         C = 32;
-        while (C < target && C < 2048) C <<= 1;
+        while (C < target && C < 256) C <<= 1;
     }
+    C = std::max<int32_t>(4, (C + 3) & ~3);
     int64_t max_chunks = 0;
     for (int n = 0; n < c->N; ++n) {
         HQ_TRY(build_partition(c, n, C));
@@ -451,13 +898,17 @@ hoqri_status passes_init(hoqri_ctx *c) {
     const int64_t want = ceil_div(std::max<int64_t>(max_chunks, 1), GEN_WARPS);
     c->pass_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 4));
     c->core_grid = c->pass_grid;
+    // the register-tiled kernels run at most FAST_MAX_CTAS_PER_SM resident CTAs per SM
+    c->core_grid_fast = c->num_sms * FAST_MAX_CTAS_PER_SM;
+    c->pass_grid_fast = c->core_grid_fast;
     int maxK = 1;
     for (int n = 0; n < c->N; ++n) maxK = std::max(maxK, (int)c->K[n]);
     // core partials [grid][P]; also holds G_(n) for the TTMcTC pass
-    c->core_part_bytes = (int64_t)std::max(c->core_grid, 1) * c->P * (int64_t)c->rsize;
+    const int gmax = std::max(std::max(c->core_grid, c->core_grid_fast), 1);
+    c->core_part_bytes = (int64_t)gmax * c->P * (int64_t)c->rsize;
     HQ_TRY(dalloc(c, &c->core_part, c->core_part_bytes));
-    // per-chunk partial rows [nchunks][2][Kn], or per-warp core accumulators
-    int64_t ab = std::max<int64_t>(max_chunks, 1) * 2 * maxK * (int64_t)c->rsize;
+    // per-chunk partial rows [nchunks][Kn], or per-warp core accumulators of the generic kernel
+    int64_t ab = std::max<int64_t>(max_chunks, 1) * maxK * (int64_t)c->rsize;
     for (int n = 0; n < c->N; ++n) {
         // same test as core_pass_t: does the per-warp accumulator fit in shared memory?
         int64_t rtot = 0, Pm = 1;

@@ -9,7 +9,8 @@
 //    the permutation perm_n, the other modes' indices and the values gathered
 //    into that order (structure of arrays), and the row descriptors: the
 //    non-empty mode-n slices I^(n)_{i_n} of Table 1 as (row_id, row_ptr).
-// 5. The partition of each sorted stream into warp tasks of C nonzeros.
+// 5. The partition of each sorted stream into warp tasks: whole rows packed
+//    up to C nonzeros per task, rows longer than C cut into pieces.
 //
 // Sorting and compaction use CUB (CUDA's header library); everything here runs
 // once per tensor, outside the iteration.
@@ -154,24 +155,6 @@ __global__ void k_row_desc(const uint32_t *keys, const int32_t *head, const int3
 }
 
 __global__ void k_set_last(int64_t *row_ptr, int64_t R, int64_t n) { row_ptr[R] = n; }
-
-// chunk_row[c] = largest r with row_ptr[r] <= c*C
-__global__ void k_chunk_rows(const int64_t *row_ptr, int64_t R, int64_t nchunks, int32_t C, int32_t *chunk_row) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nchunks; c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t pos = c * (int64_t)C;
-        int64_t lo = 0, hi = R - 1;
-        while (lo < hi) {
-            int64_t mid = (lo + hi + 1) >> 1;
-            if (row_ptr[mid] <= pos) lo = mid; else hi = mid - 1;
-        }
-        chunk_row[c] = (int32_t)lo;
-    }
-}
-
-__global__ void k_split_flags(const int64_t *row_ptr, int64_t R, int32_t C, char *flag) {
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
-        flag[r] = (row_ptr[r] / C) != ((row_ptr[r + 1] - 1) / C);
-}
 
 // RAII holder for set-up temporaries
 struct Tmp {
@@ -336,10 +319,10 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
     for (int n = 0; n < N; ++n) {
         ModeStore &M = c->ms[n];
         HQ_TRY(dalloc(c, (void **)&M.perm, std::max<int64_t>(nu, 1) * sizeof(int32_t)));
-        HQ_TRY(dalloc(c, &M.vals, std::max<int64_t>(nu, 1) * sizeof(T)));
+        HQ_TRY(dalloc(c, &M.vals, (nu + 16) * sizeof(T)));
         IdxPackW ow{};
         for (int j = 0; j < N - 1; ++j) {
-            HQ_TRY(dalloc(c, (void **)&M.oidx[j], std::max<int64_t>(nu, 1) * sizeof(int32_t)));
+            HQ_TRY(dalloc(c, (void **)&M.oidx[j], (nu + 16) * sizeof(int32_t)));
             ow.p[j] = M.oidx[j];
         }
         int64_t R = 0;
@@ -378,41 +361,60 @@ hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const vo
 hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C) {
     ModeStore &M = c->ms[n];
     cudaStream_t st = c->stream;
+    dfree(M.chunk_start);
     dfree(M.chunk_row);
-    dfree(M.split_row);
+    dfree(M.big);
+    M.chunk_start = nullptr;
     M.chunk_row = nullptr;
-    M.split_row = nullptr;
+    M.big = nullptr;
     M.C = C;
-    M.nchunks = ceil_div(c->nnz, C);
-    M.nsplit = 0;
-    HQ_TRY(dalloc(c, (void **)&M.chunk_row, std::max<int64_t>(M.nchunks, 1) * sizeof(int32_t)));
-    if (M.nchunks == 0 || M.R == 0) {
-        HQ_TRY(dalloc(c, (void **)&M.split_row, sizeof(int32_t)));
-        return HOQRI_OK;
-    }
-    k_chunk_rows<<<grid_for(M.nchunks), TPB, 0, st>>>(M.row_ptr, M.R, M.nchunks, C, M.chunk_row);
-    Tmp tmp;
-    char *flag;
-    int32_t *sel, *it;
-    int *nsel;
-    HQ_TRY(tmp.get(&flag, M.R));
-    HQ_TRY(tmp.get(&sel, M.R));
-    HQ_TRY(tmp.get(&it, M.R));
-    HQ_TRY(tmp.get(&nsel, 1));
-    k_split_flags<<<grid_for(M.R), TPB, 0, st>>>(M.row_ptr, M.R, C, flag);
-    k_iota<<<grid_for(M.R), TPB, 0, st>>>(it, M.R);
-    size_t tb = 0;
-    HQ_CUDA(cub::DeviceSelect::Flagged(nullptr, tb, it, flag, sel, nsel, (int)M.R, st));
-    char *t;
-    HQ_TRY(tmp.get(&t, tb));
-    HQ_CUDA(cub::DeviceSelect::Flagged(t, tb, it, flag, sel, nsel, (int)M.R, st));
-    int hn = 0;
-    HQ_CUDA(cudaMemcpyAsync(&hn, nsel, sizeof(int), cudaMemcpyDeviceToHost, st));
+    std::vector<int64_t> rp(M.R + 1);
+    HQ_CUDA(cudaMemcpyAsync(rp.data(), M.row_ptr, (M.R + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     HQ_CUDA(cudaStreamSynchronize(st));
-    M.nsplit = hn;
-    HQ_TRY(dalloc(c, (void **)&M.split_row, std::max<int64_t>(hn, 1) * sizeof(int32_t)));
-    if (hn > 0) HQ_CUDA(cudaMemcpyAsync(M.split_row, sel, hn * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
-    HQ_CUDA(cudaGetLastError());
+    std::vector<int64_t> starts;
+    std::vector<int32_t> crow, big;
+    int64_t cur_start = 0, cur_len = 0;
+    int32_t cur_row = 0;
+    auto close = [&]() {
+        if (cur_len > 0) {
+            starts.push_back(cur_start);
+            crow.push_back(cur_row);
+            cur_len = 0;
+        }
+    };
+    for (int64_t r = 0; r < M.R; ++r) {
+        const int64_t len = rp[r + 1] - rp[r];
+        if (len > C) {
+            close();
+            const int64_t np = (len + C - 1) / C;
+            big.push_back((int32_t)r);
+            big.push_back((int32_t)starts.size());
+            for (int64_t q = 0; q < np; ++q) {
+                starts.push_back(rp[r] + (len * q) / np);
+                crow.push_back((int32_t)r);
+            }
+            big.push_back((int32_t)starts.size() - 1);
+        } else {
+            if (cur_len + len > C) close();
+            if (cur_len == 0) {
+                cur_start = rp[r];
+                cur_row = (int32_t)r;
+            }
+            cur_len += len;
+        }
+    }
+    close();
+    M.nchunks = (int64_t)starts.size();
+    starts.push_back(c->nnz);
+    M.nbig = (int64_t)big.size() / 3;
+    HQ_TRY(dalloc(c, (void **)&M.chunk_start, starts.size() * sizeof(int64_t)));
+    HQ_TRY(dalloc(c, (void **)&M.chunk_row, std::max<size_t>(crow.size(), 1) * sizeof(int32_t)));
+    HQ_TRY(dalloc(c, (void **)&M.big, std::max<size_t>(big.size(), 1) * sizeof(int32_t)));
+    HQ_CUDA(cudaMemcpyAsync(M.chunk_start, starts.data(), starts.size() * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    if (!crow.empty())
+        HQ_CUDA(cudaMemcpyAsync(M.chunk_row, crow.data(), crow.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    if (!big.empty())
+        HQ_CUDA(cudaMemcpyAsync(M.big, big.data(), big.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     HQ_CUDA(cudaStreamSynchronize(st));
     return HOQRI_OK;
 }
