@@ -77,7 +77,10 @@ typedef struct {
     int32_t chunk_nnz;  /* nonzeros per warp task; 0 = chosen by the library */
     int32_t autotune;   /* 1: time the candidate chunk sizes once at create */
     int32_t use_graphs; /* 1: hoqri_iterate replays one sweep as a CUDA graph */
-    int32_t reserved0;
+    int32_t one_stream; /* 0/1: FP32 modes with a register-tile plan stream their nonzeros
+                           once per block update and keep Y_(n) (R_n x P_{-n} floats) for
+                           the core G = U_n^T Y_(n); 2: the paper's O(IK) memory form
+                           (separate core pass, no Y) */
     uint64_t seed;      /* seed of the initial factors when U0 is NULL */
     double tol;         /* hoqri_run: stop when |r_t - r_{t-1}| < tol (0: never) */
 } hoqri_options;

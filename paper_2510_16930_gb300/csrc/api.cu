@@ -90,6 +90,16 @@ static void destroy_impl(hoqri_ctx *c) {
         dfree(M.chunk_start);
         dfree(M.chunk_row);
         dfree(M.big);
+        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.hidx[j]);
+        dfree(M.hvals);
+        dfree(M.lrp);
+        dfree(M.lrow);
+        dfree(M.sbase);
+        dfree(M.srow);
+        dfree(M.item_s);
+        dfree(M.item_e);
+        dfree(M.item_aux);
+        dfree(M.span);
         dfree(c->U[n]);
     }
     dfree(c->G);
@@ -102,6 +112,8 @@ static void destroy_impl(hoqri_ctx *c) {
     dfree(c->qr_small);
     dfree(c->qr_work);
     dfree(c->gnorm_part);
+    dfree(c->Y);
+    dfree(c->ypart);
     cudaGetLastError();
     delete c;
 }
@@ -176,6 +188,42 @@ static hoqri_status check_mode(hoqri_ctx *c, int32_t mode) {
         return HOQRI_ERR_INVALID;
     }
     return HOQRI_OK;
+}
+
+// G <- X x {U^T} with the current factors, computed from mode m's stream.
+static hoqri_status refresh_core(hoqri_ctx *c, int m, double *slot) {
+    if (hyb_mode(c, m)) {
+        cudaEvent_t e0 = nullptr;
+        HQ_TRY(prof_begin(c, 0, &e0));
+        HQ_TRY(hyb_pass(c, m, nullptr, nullptr, true));
+        int nb = 0;
+        HQ_TRY(hyb_core_partials(c, m, &nb));
+        HQ_TRY(core_reduce(c, m, nb, c->G, slot));
+        return prof_end(c, 0, e0);
+    }
+    return core_pass(c, m, c->G, slot);
+}
+
+// A <- TTMcTC(X, {U}, n) with the current core; keep_y also stores Y_(n).
+static hoqri_status ttmctc_block(hoqri_ctx *c, int n, void *A, bool keep_y) {
+    if (hyb_mode(c, n)) {
+        cudaEvent_t e0 = nullptr;
+        HQ_TRY(prof_begin(c, 1, &e0));
+        HQ_TRY(unfold_core(c, n, c->G, c->core_part));
+        HQ_TRY(hyb_pass(c, n, (const float *)c->core_part, (float *)A, keep_y));
+        return prof_end(c, 1, e0);
+    }
+    return ttmctc_pass(c, n, c->G, A);
+}
+
+// G <- U_n^T Y_(n) after the QR of mode n (Y_(n) from the preceding ttmctc_block).
+static hoqri_status core_from_y(hoqri_ctx *c, int n, double *slot) {
+    cudaEvent_t e0 = nullptr;
+    HQ_TRY(prof_begin(c, 0, &e0));
+    int nb = 0;
+    HQ_TRY(hyb_core_partials(c, n, &nb));
+    HQ_TRY(core_reduce(c, n, nb, c->G, slot));
+    return prof_end(c, 0, e0);
 }
 
 }  // namespace hoqri
@@ -368,7 +416,7 @@ hoqri_status hoqri_core(hoqri_ctx *c, void *G_out) {
         set_error("hoqri_core: G_out is NULL");
         return HOQRI_ERR_INVALID;
     }
-    HQ_TRY(core_pass(c, 0, c->G, nullptr));
+    HQ_TRY(refresh_core(c, 0, nullptr));
     return copy_out(c, G_out, c->G, c->P * c->rsize);
 }
 
@@ -379,8 +427,8 @@ hoqri_status hoqri_ttmctc(hoqri_ctx *c, int32_t mode, void *A_out) {
         set_error("hoqri_ttmctc: A_out is NULL");
         return HOQRI_ERR_INVALID;
     }
-    HQ_TRY(core_pass(c, mode, c->G, nullptr));
-    HQ_TRY(ttmctc_pass(c, mode, c->G, c->A));
+    HQ_TRY(refresh_core(c, mode, nullptr));
+    HQ_TRY(ttmctc_block(c, mode, c->A, false));
     return copy_out(c, A_out, c->A, c->dims[mode] * c->K[mode] * c->rsize);
 }
 
@@ -431,14 +479,18 @@ hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
         HQ_CUDA(cudaMemcpyAsync(&before, c->dflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
         HQ_CUDA(cudaStreamSynchronize(c->stream));
     }
+    // slot 2 + k holds ||G||^2 after k block updates (k = 0: the initial core)
+    HQ_TRY(refresh_core(c, 0, c->dnorm + 2));
     for (int t = 0; t < iters; ++t) {
         for (int n = 0; n < N; ++n) {
-            HQ_TRY(core_pass(c, n, c->G, c->dnorm + 2 + (int64_t)t * N + n));
-            HQ_TRY(ttmctc_pass(c, n, c->G, c->A));
+            double *slot = c->dnorm + 2 + (int64_t)t * N + n + 1;
+            const bool one = hyb_mode(c, n);
+            HQ_TRY(ttmctc_block(c, n, c->A, one));
             HQ_TRY(orthonormalize(c, n, c->A, c->U[n]));
+            if (one) HQ_TRY(core_from_y(c, n, slot));
+            else HQ_TRY(refresh_core(c, (n + 1) % N, slot));
         }
     }
-    HQ_TRY(core_pass(c, 0, c->G, c->dnorm + 2 + (int64_t)iters * N));
     if (resid_hist || c->opt.qr_kind == 2) {
         std::vector<double> h(2 + (size_t)iters * N + 1);
         HQ_CUDA(cudaMemcpyAsync(h.data(), c->dnorm, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

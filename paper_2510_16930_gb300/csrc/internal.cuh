@@ -58,6 +58,29 @@ struct ModeStore {
     int32_t *chunk_row = nullptr;        // [nchunks] first row (index into row_id) of each chunk
     int64_t nbig = 0;
     int32_t *big = nullptr;              // [3*nbig] (row, first chunk, last chunk) of each big row
+
+    // Hybrid copy of the same nonzeros for the register-tiled FP32 kernels:
+    // rows longer than Lshort stay contiguous (row order) at the front; the
+    // other rows are sorted by length and stored as slices of 8 rows, element
+    // (step s, row g) of slice j at sbase[j] + 8*s + g, shorter rows padded with
+    // (index 0, value 0) entries.  Work items: long tasks (contiguous ranges of
+    // the long part, cut every ~T nonzeros at multiples of 8) then slice tasks
+    // (runs of consecutive slices).
+    bool hyb = false;
+    int64_t htotal = 0;                  // stored elements (with padding)
+    int32_t *hidx[HOQRI_MAXN - 1] = {};
+    void *hvals = nullptr;
+    int64_t nlong = 0;                   // rows in the long part
+    int64_t *lrp = nullptr;              // [nlong+1] offsets of the long rows
+    int32_t *lrow = nullptr;             // [nlong] compact row index r (into row_id)
+    int64_t nslice = 0;
+    int64_t *sbase = nullptr;            // [nslice+1]
+    int32_t *srow = nullptr;             // [8*nslice] compact row index, -1 for padding rows
+    int64_t nitem = 0, nitem_long = 0;
+    int64_t *item_s = nullptr, *item_e = nullptr;  // [nitem] element ranges
+    int32_t *item_aux = nullptr;         // long: first long row; slice task: first slice
+    int64_t nspan = 0;
+    int32_t *span = nullptr;             // [3*nspan] (long row j, first task, last task) of rows cut by tasks
 };
 
 struct Workspace;  // defined in the pass unit
@@ -96,6 +119,10 @@ struct hoqri_ctx {
     double *qr_small = nullptr;         // K x K FP64 workspace (Rinv) and norms
     double *qr_work = nullptr;          // Householder fallback workspace (max I*K doubles)
     double *gnorm_part = nullptr;       // block partials of ||G||^2
+    float *Y = nullptr;                 // rows y_i of Y_(n) for the modes using the hybrid kernels
+    int64_t Y_bytes = 0;
+    float *ypart = nullptr;             // [nitem_long][2][P_{-n}] pieces of rows cut by long tasks
+    int64_t ypart_bytes = 0;
     int core_grid = 0;                  // CTAs of the core pass (fixed per context)
     int pass_grid = 0;
     int core_grid_fast = 0;             // the same for the register-tiled FP32 kernels
@@ -126,8 +153,26 @@ void dfree(void *p);
 // setup (setup.cu)
 hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw);
 hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C);
+hoqri_status build_hybrid(hoqri_ctx *c, int n, int64_t Lshort, int64_t T, int SW);
+
+// register-tile plan of the FP32 kernels for mode n (passes.cu)
+struct FastTile {
+    bool ok = false;
+    int nm1 = 0, TL = 0, TV = 0, GL = 0, GV = 0, lpn = 0;
+    int Ka = 0, Kb = 0, Kl = 0, Pm = 0;
+};
+bool fast_tile(const hoqri_ctx *c, int n, FastTile *out);
 
 // passes (passes.cu)
+hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *normG2_slot);
+hoqri_status unfold_core(hoqri_ctx *c, int n, const void *G, void *Gn);
+
+// one-stream FP32 passes on the hybrid layout (hybrid.cu)
+bool hyb_mode(const hoqri_ctx *c, int n);
+hoqri_status hyb_pass(hoqri_ctx *c, int n, const float *Gn, float *A_out, bool write_y);
+hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk);
+size_t hyb_smem_need(const hoqri_ctx *c, int n, bool wa);
+size_t hyb_smem_cap();
 hoqri_status passes_init(hoqri_ctx *c);
 hoqri_status core_pass(hoqri_ctx *c, int n, void *G_out, double *normG2_slot);
 hoqri_status ttmctc_pass(hoqri_ctx *c, int n, const void *G, void *A_out);

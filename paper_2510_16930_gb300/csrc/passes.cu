@@ -303,7 +303,7 @@ __device__ __forceinline__ void ldg_vec(float (&d)[TN], const float *p) {
 // single ka: scalar from Ua, z-rows from Ub, v-rows from Uc.
 template <int NM1, int TL, int TV, bool CORE>
 __global__ void __launch_bounds__(256) k_pass_fast(FastArgs a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     float *smf = reinterpret_cast<float *>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);  // 2 per warp, at the start
     const int lane = threadIdx.x & 31;
@@ -605,16 +605,10 @@ int pl_for(int Pm) {
 
 // ---- fast-path plan for mode n
 
-struct FastPlan {
-    bool ok = false;
-    int nm1 = 0, TL = 0, TV = 0, GL = 0, GV = 0, lpn = 0;
-    int Ka = 0, Kb = 0, Kl = 0, Pm = 0;
-};
-
 bool pow2_ge4(int k) { return k >= 4 && k <= 64 && (k & (k - 1)) == 0; }
 
-FastPlan fast_plan(const hoqri_ctx *c, int n) {
-    FastPlan p;
+FastTile fast_plan(const hoqri_ctx *c, int n) {
+    FastTile p;
     if (c->prec != HOQRI_FP32 || (c->N != 3 && c->N != 4)) return p;
     int Ko[3], j = 0;
     for (int m = 0; m < c->N; ++m)
@@ -708,7 +702,7 @@ struct FastLaunch {
     int gs_off = 0, w_off = 0, w_stride = 0;
 };
 
-FastLaunch fast_launch(const hoqri_ctx *c, int n, const FastPlan &p, bool core) {
+FastLaunch fast_launch(const hoqri_ctx *c, int n, const FastTile &p, bool core) {
     FastLaunch L;
     const int Kn = c->K[n];
     const int KnPm = Kn * p.Pm;
@@ -728,7 +722,7 @@ FastLaunch fast_launch(const hoqri_ctx *c, int n, const FastPlan &p, bool core) 
 // capped by the number of warp tasks; it depends only on the device, kernel
 // and shape, so a context always uses the same grid (fixed summation order).
 template <int NM1, bool CORE>
-hoqri_status launch_fast_nm1(hoqri_ctx *c, const FastPlan &p, FastArgs &a, const FastLaunch &L, int *grid) {
+hoqri_status launch_fast_nm1(hoqri_ctx *c, const FastTile &p, FastArgs &a, const FastLaunch &L, int *grid) {
 #define HQ_FAST(TLV, TVV)                                                                                  \
     if (p.TL == TLV && p.TV == TVV) {                                                                      \
         auto kern = k_pass_fast<NM1, TLV, TVV, CORE>;                                                      \
@@ -753,7 +747,7 @@ hoqri_status launch_fast_nm1(hoqri_ctx *c, const FastPlan &p, FastArgs &a, const
 }
 
 template <bool CORE>
-hoqri_status launch_fast(hoqri_ctx *c, int n, const FastPlan &p, const float *Gn, float *A_out, int *grid) {
+hoqri_status launch_fast(hoqri_ctx *c, int n, const FastTile &p, const float *Gn, float *A_out, int *grid) {
     const ModeStore &M = c->ms[n];
     FastArgs a{};
     a.Kn = c->K[n];
@@ -796,8 +790,8 @@ hoqri_status launch_fast(hoqri_ctx *c, int n, const FastPlan &p, const float *Gn
     return launch_fast_nm1<3, CORE>(c, p, a, L, grid);
 }
 
-bool use_fast(const hoqri_ctx *c, int n, bool core, FastPlan *out) {
-    FastPlan p = fast_plan(c, n);
+bool use_fast(const hoqri_ctx *c, int n, bool core, FastTile *out) {
+    FastTile p = fast_plan(c, n);
     if (!p.ok || c->ms[n].C % 4 != 0) return false;
     FastLaunch L = fast_launch(c, n, p, core);
     if (L.smem > SMEM_CAP) return false;
@@ -811,7 +805,7 @@ hoqri_status core_pass_t(hoqri_ctx *c, int n, void *G_out, double *normG2_slot) 
     fill_common<T>(c, n, a);
     const int KnPm = a.Kn * a.Pm;
     int grid = c->core_grid;
-    FastPlan fp;
+    FastTile fp;
     if (std::is_same<T, float>::value && use_fast(c, n, true, &fp)) {
         HQ_TRY(launch_fast<true>(c, n, fp, nullptr, nullptr, &grid));
     } else {
@@ -854,7 +848,7 @@ hoqri_status ttmctc_pass_t(hoqri_ctx *c, int n, const void *G, void *A_out) {
         set_error("TTMcTC pass: partial-row workspace too small");
         return HOQRI_ERR_UNSUPPORTED;
     }
-    FastPlan fp;
+    FastTile fp;
     if (std::is_same<T, float>::value && use_fast(c, n, false, &fp)) {
         int grid = 0;
         HQ_TRY(launch_fast<false>(c, n, fp, (const float *)Gn, (float *)A_out, &grid));
@@ -879,6 +873,42 @@ hoqri_status ttmctc_pass_t(hoqri_ctx *c, int n, const void *G, void *A_out) {
 }  // namespace
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+bool fast_tile(const hoqri_ctx *c, int n, FastTile *out) {
+    FastTile p = fast_plan(c, n);
+    if (!p.ok) return false;
+    *out = p;
+    return true;
+}
+
+hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *normG2_slot) {
+    CoreMap m = core_map(c, n);
+    const int KnPm = m.Kn * m.Pm;
+    const int rb = std::max(1, std::min(64, (KnPm + RED_TPB - 1) / RED_TPB));
+    if (c->prec == HOQRI_FP64)
+        k_core_reduce<double><<<rb, RED_TPB, 0, c->stream>>>((const double *)c->core_part, nblk, m, (double *)G_out,
+                                                              c->gnorm_part);
+    else
+        k_core_reduce<float><<<rb, RED_TPB, 0, c->stream>>>((const float *)c->core_part, nblk, m, (float *)G_out,
+                                                            c->gnorm_part);
+    k_sum_into<<<1, 32, 0, c->stream>>>(c->gnorm_part, rb, c->dnorm + 1, normG2_slot);
+    c->nlaunch += 2;
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+hoqri_status unfold_core(hoqri_ctx *c, int n, const void *G, void *Gn) {
+    CoreMap m = core_map(c, n);
+    const int KnPm = m.Kn * m.Pm;
+    const int g = std::max(1, std::min(64, (KnPm + 255) / 256));
+    if (c->prec == HOQRI_FP64)
+        k_core_to_unfolded<double><<<g, 256, 0, c->stream>>>((const double *)G, m, (double *)Gn);
+    else
+        k_core_to_unfolded<float><<<g, 256, 0, c->stream>>>((const float *)G, m, (float *)Gn);
+    c->nlaunch++;
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
 
 // Sizes the partition and the scratch buffers of the passes.
 hoqri_status passes_init(hoqri_ctx *c) {
@@ -922,8 +952,29 @@ hoqri_status passes_init(hoqri_ctx *c) {
         if ((int64_t)GEN_WARPS * wst * (int64_t)c->rsize > (int64_t)SMEM_CAP)
             ab = std::max(ab, (int64_t)c->core_grid * GEN_WARPS * c->P * (int64_t)c->rsize);
     }
+    // hybrid layout + dense Y for the FP32 modes with a register-tile plan
+    int64_t ybytes = 0, ypb = 0;
+    const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 32)));
+    const int64_t T32 = (Tt + 31) & ~(int64_t)31;
+    for (int n = 0; n < c->N; ++n) {
+        FastTile p;
+        if (!fast_tile(c, n, &p) || c->opt.one_stream == 2) continue;
+        if (hyb_smem_need(c, n, true) > hyb_smem_cap()) continue;
+        HQ_TRY(build_hybrid(c, n, 256, T32, 32 / p.lpn));
+        const ModeStore &M = c->ms[n];
+        ab = std::max<int64_t>(ab, std::max<int64_t>(M.nitem_long, 1) * 2 * c->K[n] * (int64_t)c->rsize);
+        ybytes = std::max<int64_t>(ybytes, M.R * (int64_t)p.Pm * 4);
+        ypb = std::max<int64_t>(ypb, std::max<int64_t>(M.nitem_long, 1) * 2 * (int64_t)p.Pm * 4);
+    }
     c->a_part_bytes = ab;
     HQ_TRY(dalloc(c, &c->a_part, c->a_part_bytes));
+    const int64_t ybudget = (int64_t)8 << 30;
+    if (ybytes > 0 && c->opt.one_stream != 2 && ybytes <= ybudget) {
+        HQ_TRY(dalloc(c, (void **)&c->Y, ybytes));
+        c->Y_bytes = ybytes;
+        HQ_TRY(dalloc(c, (void **)&c->ypart, ypb));
+        c->ypart_bytes = ypb;
+    }
     HQ_TRY(dalloc(c, (void **)&c->gnorm_part, 64 * sizeof(double)));
     return HOQRI_OK;
 }

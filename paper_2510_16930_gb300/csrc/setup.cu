@@ -17,6 +17,7 @@
 #include <cub/cub.cuh>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -155,6 +156,17 @@ __global__ void k_row_desc(const uint32_t *keys, const int32_t *head, const int3
 }
 
 __global__ void k_set_last(int64_t *row_ptr, int64_t R, int64_t n) { row_ptr[R] = n; }
+
+// hybrid copy: dst[p] = src[map[p]] (map -1: padding entry, index 0 and value 0)
+template <typename T>
+__global__ void k_hyb_gather(IdxPack src, IdxPackW dst, int nm1, const int32_t *map, int64_t total, const T *vsrc,
+                             T *vdst) {
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = map[p];
+        for (int j = 0; j < nm1; ++j) dst.p[j][p] = q >= 0 ? src.p[j][q] : 0;
+        vdst[p] = q >= 0 ? vsrc[q] : T(0);
+    }
+}
 
 // RAII holder for set-up temporaries
 struct Tmp {
@@ -417,6 +429,120 @@ hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C) {
         HQ_CUDA(cudaMemcpyAsync(M.big, big.data(), big.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     HQ_CUDA(cudaStreamSynchronize(st));
     return HOQRI_OK;
+}
+
+template <typename T>
+static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t T8, int SW) {
+    ModeStore &M = c->ms[n];
+    cudaStream_t st = c->stream;
+    const int nm1 = c->N - 1;
+    std::vector<int64_t> rp(M.R + 1);
+    HQ_CUDA(cudaMemcpyAsync(rp.data(), M.row_ptr, (M.R + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    HQ_CUDA(cudaStreamSynchronize(st));
+    std::vector<int32_t> lrow, srt;
+    for (int64_t r = 0; r < M.R; ++r) {
+        if (rp[r + 1] - rp[r] > Lshort) lrow.push_back((int32_t)r);
+        else srt.push_back((int32_t)r);
+    }
+    std::stable_sort(srt.begin(), srt.end(),
+                     [&](int32_t a, int32_t b) { return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]); });
+    const int64_t nlong = (int64_t)lrow.size();
+    std::vector<int64_t> lrp(nlong + 1, 0);
+    for (int64_t j = 0; j < nlong; ++j) lrp[j + 1] = lrp[j] + (rp[lrow[j] + 1] - rp[lrow[j]]);
+    const int64_t total_long = lrp[nlong];
+    const int64_t nslice = ((int64_t)srt.size() + SW - 1) / SW;
+    std::vector<int64_t> sbase(nslice + 1);
+    std::vector<int32_t> srow((size_t)SW * nslice, -1);
+    sbase[0] = (total_long + 31) & ~(int64_t)31;
+    for (int64_t j = 0; j < nslice; ++j) {
+        for (int g = 0; g < SW && SW * j + g < (int64_t)srt.size(); ++g) srow[SW * j + g] = srt[SW * j + g];
+        const int64_t L = rp[srow[SW * j] + 1] - rp[srow[SW * j]];
+        // slice sizes stay multiples of 4 elements so every slice starts 16-byte aligned
+        sbase[j + 1] = sbase[j] + ((SW * L + 3) & ~(int64_t)3);
+    }
+    const int64_t total = sbase[nslice];
+    std::vector<int32_t> map(total + 16, -1);
+    for (int64_t j = 0; j < nlong; ++j)
+        for (int64_t q = 0; q < lrp[j + 1] - lrp[j]; ++q) map[lrp[j] + q] = (int32_t)(rp[lrow[j]] + q);
+    for (int64_t j = 0; j < nslice; ++j)
+        for (int g = 0; g < SW; ++g) {
+            const int32_t r = srow[SW * j + g];
+            if (r < 0) continue;
+            for (int64_t q = 0; q < rp[r + 1] - rp[r]; ++q) map[sbase[j] + SW * q + g] = (int32_t)(rp[r] + q);
+        }
+    // work items: long tasks of T8 elements, then runs of slices of about T8 elements
+    std::vector<int64_t> is, ie;
+    std::vector<int32_t> ia, span;
+    {
+        int64_t j = 0;
+        for (int64_t t0 = 0; t0 < total_long; t0 += T8) {
+            while (j + 1 < nlong && lrp[j + 1] <= t0) ++j;
+            is.push_back(t0);
+            ie.push_back(std::min(t0 + T8, total_long));
+            ia.push_back((int32_t)j);
+        }
+        for (int64_t jj = 0; jj < nlong; ++jj) {
+            const int64_t a = lrp[jj] / T8, b = (lrp[jj + 1] - 1) / T8;
+            if (a != b) {
+                span.push_back((int32_t)jj);
+                span.push_back((int32_t)a);
+                span.push_back((int32_t)b);
+            }
+        }
+    }
+    const int64_t nitem_long = (int64_t)is.size();
+    for (int64_t j = 0; j < nslice;) {
+        int64_t k = j;
+        while (k < nslice && sbase[k] - sbase[j] < T8) ++k;
+        is.push_back(sbase[j]);
+        ie.push_back(sbase[k]);
+        ia.push_back((int32_t)j);
+        j = k;
+    }
+    M.hyb = true;
+    M.htotal = total;
+    M.nlong = nlong;
+    M.nslice = nslice;
+    M.nitem_long = nitem_long;
+    M.nitem = (int64_t)is.size();
+    M.nspan = (int64_t)span.size() / 3;
+    Tmp tmp;
+    int32_t *dmap;
+    HQ_TRY(tmp.get(&dmap, total + 16));
+    HQ_CUDA(cudaMemcpyAsync(dmap, map.data(), (total + 16) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    IdxPack src{};
+    IdxPackW dst{};
+    for (int j = 0; j < nm1; ++j) {
+        HQ_TRY(dalloc(c, (void **)&M.hidx[j], (total + 16) * sizeof(int32_t)));
+        src.p[j] = M.oidx[j];
+        dst.p[j] = M.hidx[j];
+    }
+    HQ_TRY(dalloc(c, &M.hvals, (total + 16) * sizeof(T)));
+    k_hyb_gather<T><<<std::min(grid_for(total + 16), c->num_sms * 8), TPB, 0, st>>>(
+        src, dst, nm1, dmap, total + 16, (const T *)M.vals, (T *)M.hvals);
+    auto up = [&](auto **d, const auto &v) -> hoqri_status {
+        using E = typename std::decay<decltype(v[0])>::type;
+        HQ_TRY(dalloc(c, (void **)d, std::max<size_t>(v.size(), 1) * sizeof(E)));
+        if (!v.empty()) HQ_CUDA(cudaMemcpyAsync(*d, v.data(), v.size() * sizeof(E), cudaMemcpyHostToDevice, st));
+        return HOQRI_OK;
+    };
+    HQ_TRY(up(&M.lrp, lrp));
+    HQ_TRY(up(&M.lrow, lrow));
+    HQ_TRY(up(&M.sbase, sbase));
+    HQ_TRY(up(&M.srow, srow));
+    HQ_TRY(up(&M.item_s, is));
+    HQ_TRY(up(&M.item_e, ie));
+    HQ_TRY(up(&M.item_aux, ia));
+    HQ_TRY(up(&M.span, span));
+    HQ_CUDA(cudaGetLastError());
+    HQ_CUDA(cudaStreamSynchronize(st));
+    return HOQRI_OK;
+}
+
+hoqri_status build_hybrid(hoqri_ctx *c, int n, int64_t Lshort, int64_t T, int SW) {
+    const int64_t T32 = std::max<int64_t>(32, (T + 31) & ~(int64_t)31);
+    if (c->prec == HOQRI_FP64) return build_hybrid_t<double>(c, n, Lshort, T32, SW);
+    return build_hybrid_t<float>(c, n, Lshort, T32, SW);
 }
 
 }  // namespace hoqri

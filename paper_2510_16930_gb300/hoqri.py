@@ -30,7 +30,7 @@ SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc"
 
 class hoqri_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("qr_kind", C.c_int32), ("chunk_nnz", C.c_int32), ("autotune", C.c_int32),
-                ("use_graphs", C.c_int32), ("reserved0", C.c_int32), ("seed", C.c_uint64), ("tol", C.c_double)]
+                ("use_graphs", C.c_int32), ("one_stream", C.c_int32), ("seed", C.c_uint64), ("tol", C.c_double)]
 
 
 class HoqriError(RuntimeError):

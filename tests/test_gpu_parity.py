@@ -33,6 +33,10 @@ SHAPES = [
     ((500, 400), (7, 7), 4000, "uniform"),                  # order 2 (matrix)
     ((64, 50, 40), (1, 1, 1), 2000, "uniform"),            # rank one
     ((60, 50, 40), (8, 16, 12), 4000, "zipf"),             # P_{-n} up to 192, mixed K
+    ((60, 40, 30, 20), (8, 8, 8, 8), 20_000, "zipf"),      # order 4, K = 8 (register tiles)
+    ((40, 30, 20, 16), (4, 8, 4, 8), 6000, "uniform"),      # order 4, mixed power-of-two K
+    ((500, 300, 200), (32, 32, 32), 8000, "zipf"),         # K = 32: 1024-element y per row
+    ((400, 300, 200), (4, 16, 8), 8000, "zipf"),           # small and mixed tiles
 ]
 
 
