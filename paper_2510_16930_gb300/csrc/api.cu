@@ -195,7 +195,7 @@ static hoqri_status refresh_core(hoqri_ctx *c, int m, double *slot) {
     if (hyb_mode(c, m)) {
         cudaEvent_t e0 = nullptr;
         HQ_TRY(prof_begin(c, 0, &e0));
-        HQ_TRY(hyb_pass(c, m, nullptr, nullptr, true));
+        HQ_TRY(hyb_pass(c, m));
         int nb = 0;
         HQ_TRY(hyb_core_partials(c, m, &nb));
         HQ_TRY(core_reduce(c, m, nb, c->G, slot));
@@ -204,13 +204,16 @@ static hoqri_status refresh_core(hoqri_ctx *c, int m, double *slot) {
     return core_pass(c, m, c->G, slot);
 }
 
-// A <- TTMcTC(X, {U}, n) with the current core; keep_y also stores Y_(n).
+// A <- TTMcTC(X, {U}, n) with the current core; in hybrid modes Y_(n) stays in
+// c->Y for a following core_from_y.
 static hoqri_status ttmctc_block(hoqri_ctx *c, int n, void *A, bool keep_y) {
+    (void)keep_y;
     if (hyb_mode(c, n)) {
         cudaEvent_t e0 = nullptr;
         HQ_TRY(prof_begin(c, 1, &e0));
+        HQ_TRY(hyb_pass(c, n));
         HQ_TRY(unfold_core(c, n, c->G, c->core_part));
-        HQ_TRY(hyb_pass(c, n, (const float *)c->core_part, (float *)A, keep_y));
+        HQ_TRY(hyb_a_from_y(c, n, (const float *)c->core_part, (float *)A));
         return prof_end(c, 1, e0);
     }
     return ttmctc_pass(c, n, c->G, A);

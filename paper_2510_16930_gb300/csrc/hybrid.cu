@@ -23,6 +23,8 @@
 // Each window of the index/value streams (HY_W elements) is staged in shared
 // memory by TMA bulk copies completing on an mbarrier, double buffered across
 // the warp's windows; all waits are bounded.
+#include <cuda.h>
+
 #include <algorithm>
 
 #include "internal.cuh"
@@ -32,8 +34,9 @@ namespace hoqri {
 namespace {
 
 constexpr int HY_WARPS = 8;
-constexpr int HY_W = 512;           // staged elements per window (multiple of 32)
+constexpr int HY_W = 256;           // staged elements per window (multiple of 32)
 constexpr int HY_WB = HY_W + 8;     // floats per staged array
+constexpr int HY_NB = 4;            // factor-row stages in flight per warp (32 nonzeros each), power of two
 constexpr size_t HY_SMEM_CAP = 200 * 1024;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -72,22 +75,9 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
-template <int TN>
-__device__ __forceinline__ void ldg_vec(float (&d)[TN], const float *p) {
-#pragma unroll
-    for (int q = 0; q < TN / 4; ++q) {
-        const float4 t = __ldg(reinterpret_cast<const float4 *>(p) + q);
-        d[4 * q + 0] = t.x;
-        d[4 * q + 1] = t.y;
-        d[4 * q + 2] = t.z;
-        d[4 * q + 3] = t.w;
-    }
-}
-
 struct HybArgs {
-    int Kn, Pm, Kl, Ka, Kb, GV, lpn;
+    int Kn, Pm, Kl, Ka, Kb, Kc, GV, lpn;
     const int32_t *ia, *ib, *ic;
-    const float *Ua, *Ub, *Uc;
     const float *vals;
     const int32_t *row_id;
     const int64_t *lrp;
@@ -97,7 +87,12 @@ struct HybArgs {
     const int64_t *item_s, *item_e;
     const int32_t *item_aux;
     int64_t nitem, nitem_long;
-    int warps, gs_off, w_off, w_stride;
+    int bar_off, gs_off, w_off, w_stride;  // shared memory layout (bytes)
+    int meta_bytes;                        // one staged array of a window (HY_WB floats)
+    int ring_off, stage_bytes;             // gathered factor rows: NB stages per warp
+    int stage_tx;                          // bytes the gathers of one stage deliver
+    int sa, sb, sc;                        // bytes per 4-row gather slot of Ua / Ub / Uc
+    int offb, offc;                        // offsets of the Ub / Uc rows inside a stage
     const float *Gn;  // [Kn][Pm]
     float *A;
     float *Y;
@@ -106,17 +101,29 @@ struct HybArgs {
     int32_t *err;
 };
 
-template <int NM1, int TL, int TV, bool WA, bool WY>
-__global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *smf = reinterpret_cast<float *>(smem_raw);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw);
+// 4 rows (r0..r3) of a 2-D row-major factor, full width, into shared memory.
+__device__ __forceinline__ void gather4(void *dst, const CUtensorMap *tm, int r0, int r1, int r2, int r3,
+                                        uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <int NM1, int TL, int TV>
+__global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ CUtensorMap tmA,
+                                                       const __grid_constant__ CUtensorMap tmB,
+                                                       const __grid_constant__ CUtensorMap tmC, HybArgs a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int lpn = a.lpn;
-    const int NG = 32 / lpn;  // lane groups = rows per slice
-    const int g = lane / lpn;
-    const int sub = lane - g * lpn;
+    const int lg_lpn = __ffs(lpn) - 1;
+    const int NG = 32 >> lg_lpn;  // lane groups = rows per slice = nonzeros per step
+    const int lg_ng = 5 - lg_lpn;
+    const int g = lane >> lg_lpn;
+    const int sub = lane & (lpn - 1);
     const int gl = sub / a.GV;
     const int gv = sub - gl * a.GV;
     const int l0 = gl * TL;
@@ -126,33 +133,31 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         ka = l0 / a.Kb;
         kb0 = l0 - ka * a.Kb;
     }
-    const int KnPm = a.Kn * a.Pm;
-    const float *Gs = smf + a.gs_off;
-    float *wbase = smf + a.w_off + (size_t)w * a.w_stride;
     constexpr int NARR = NM1 + 1;
-    uint64_t *bar = bars + 2 * w;
+    unsigned char *wbase = smem_raw + a.w_off + (size_t)w * a.w_stride;
+    unsigned char *ring = wbase + a.ring_off;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + a.bar_off) + (size_t)w * (2 + HY_NB);
+    uint64_t *sbar = mbar + 2;
 
-    if (threadIdx.x == 0)
-        for (int q = 0; q < 2 * a.warps; ++q) mbar_init(bars + q, 1);
-    if (WA)
-        for (int p = threadIdx.x; p < KnPm; p += blockDim.x) smf[a.gs_off + p] = a.Gn[p];
+    if (lane == 0)
+        for (int q = 0; q < 2 + HY_NB; ++q) mbar_init(mbar + q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
 
-    const int64_t gw = (int64_t)blockIdx.x * a.warps + w;
-    const int64_t nw = (int64_t)gridDim.x * a.warps;
+    const int64_t gw = (int64_t)blockIdx.x * HY_WARPS + w;
+    const int64_t nw = (int64_t)gridDim.x * HY_WARPS;
 
-    auto issue = [&](int64_t p0, int64_t p1, int buf) {
+    // stage the index and value streams of window [p0, p1) into meta buffer `buf`
+    auto issue_meta = [&](int64_t p0, int64_t p1, int buf) {
         if (lane == 0) {
-            const uint32_t n4 = (uint32_t)(((p1 - p0) + 3) & ~(int64_t)3);
-            const uint32_t bytes = n4 * 4u;
-            float *dst = wbase + (size_t)buf * NARR * HY_WB;
+            const uint32_t bytes = (uint32_t)(((p1 - p0) + 3) & ~(int64_t)3) * 4u;
+            unsigned char *dst = wbase + (size_t)buf * NARR * a.meta_bytes;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(bar + buf, bytes * NARR);
-            bulk_g2s(dst, a.ia + p0, bytes, bar + buf);
-            bulk_g2s(dst + HY_WB, a.ib + p0, bytes, bar + buf);
-            if (NM1 == 3) bulk_g2s(dst + 2 * HY_WB, a.ic + p0, bytes, bar + buf);
-            bulk_g2s(dst + (NARR - 1) * HY_WB, a.vals + p0, bytes, bar + buf);
+            mbar_expect_tx(mbar + buf, bytes * NARR);
+            bulk_g2s(dst, a.ia + p0, bytes, mbar + buf);
+            bulk_g2s(dst + a.meta_bytes, a.ib + p0, bytes, mbar + buf);
+            if (NM1 == 3) bulk_g2s(dst + 2 * a.meta_bytes, a.ic + p0, bytes, mbar + buf);
+            bulk_g2s(dst + (NARR - 1) * a.meta_bytes, a.vals + p0, bytes, mbar + buf);
         }
     };
 
@@ -163,8 +168,6 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
 #pragma unroll
             for (int k = 0; k < TV; ++k) y[j][k] = 0.f;
     };
-
-    // write this lane's tile of y to dst (a P_{-n} vector)
     auto store_tile = [&](float *dst) {
 #pragma unroll
         for (int j = 0; j < TL; ++j) {
@@ -174,33 +177,15 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 p[k4] = make_float4(y[j][4 * k4], y[j][4 * k4 + 1], y[j][4 * k4 + 2], y[j][4 * k4 + 3]);
         }
     };
-
-    // partial G_(n)[kn] . y over this lane's tile
-    auto dot_tile = [&](int kn) {
-        float s = 0.f;
-#pragma unroll
-        for (int j = 0; j < TL; ++j) {
-            const float4 *gp = reinterpret_cast<const float4 *>(Gs + (size_t)kn * a.Pm + (size_t)(l0 + j) * a.Kl + v0);
-#pragma unroll
-            for (int k4 = 0; k4 < TV / 4; ++k4) {
-                const float4 gq = gp[k4];
-                s = fmaf(gq.x, y[j][4 * k4 + 0], s);
-                s = fmaf(gq.y, y[j][4 * k4 + 1], s);
-                s = fmaf(gq.z, y[j][4 * k4 + 2], s);
-                s = fmaf(gq.w, y[j][4 * k4 + 3], s);
-            }
-        }
-        return s;
-    };
-
     bool ok = true;
-    int k = 0;  // windows processed by this warp (buffer = k & 1, phase = (k >> 1) & 1)
+    int mk = 0;         // meta windows consumed by this warp
+    int gst = 0;        // factor-row stages consumed by this warp (wraps harmlessly)
     int64_t it = gw;
     int64_t p0 = it < a.nitem ? a.item_s[it] : 0;
-    if (it < a.nitem) issue(p0, min(p0 + (int64_t)HY_W, a.item_e[it]), 0);
-    int64_t j = 0;  // current long row or slice
+    if (it < a.nitem) issue_meta(p0, min(p0 + (int64_t)HY_W, a.item_e[it]), 0);
+    int64_t j = 0;
     while (it < a.nitem) {
-        const int buf = k & 1;
+        const int mbuf = mk & 1;
         const int64_t ts = a.item_s[it], te = a.item_e[it];
         const int64_t p1 = min(p0 + (int64_t)HY_W, te);
         int64_t nit = it, np0 = p0 + HY_W;
@@ -208,52 +193,107 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
             nit = it + nw;
             np0 = nit < a.nitem ? a.item_s[nit] : 0;
         }
-        if (nit < a.nitem) issue(np0, min(np0 + (int64_t)HY_W, a.item_e[nit]), buf ^ 1);
-        if (!mbar_wait(bar + buf, (uint32_t)((k >> 1) & 1), a.err)) {
+        if (nit < a.nitem) issue_meta(np0, min(np0 + (int64_t)HY_W, a.item_e[nit]), mbuf ^ 1);
+        if (!mbar_wait(mbar + mbuf, (uint32_t)((mk >> 1) & 1), a.err)) {
             ok = false;
             break;
         }
-        const float *mb = wbase + (size_t)buf * NARR * HY_WB;
+        const unsigned char *mb = wbase + (size_t)mbuf * NARR * a.meta_bytes;
         const int32_t *mia = reinterpret_cast<const int32_t *>(mb);
-        const int32_t *mib = reinterpret_cast<const int32_t *>(mb + HY_WB);
-        const int32_t *mic = reinterpret_cast<const int32_t *>(mb + 2 * HY_WB);
-        const float *mval = mb + (NARR - 1) * HY_WB;
-        auto load_nz = [&](int q, float (&z)[TL], float (&v)[TV]) {
-            const float x = mval[q];
-            if (NM1 == 2) {
-                ldg_vec<TL>(z, a.Ua + (int64_t)mia[q] * a.Ka + l0);
-                ldg_vec<TV>(v, a.Ub + (int64_t)mib[q] * a.Kl + v0);
+        const int32_t *mib = reinterpret_cast<const int32_t *>(mb + a.meta_bytes);
+        const int32_t *mic = reinterpret_cast<const int32_t *>(mb + 2 * a.meta_bytes);
+        const float *mval = reinterpret_cast<const float *>(mb + (NARR - 1) * a.meta_bytes);
+        const int len = (int)(p1 - p0);
+        const int nst = (len + 31) >> 5;
+
+        // gather the factor rows of stage s (elements 32s .. 32s+31 of the window)
+        auto issue_stage = [&](int s) {
+            const int slot = (gst + s) & (HY_NB - 1);
+            unsigned char *st = ring + (size_t)slot * a.stage_bytes;
+            __syncwarp();
+            if (lane == 0) mbar_expect_tx(sbar + slot, (uint32_t)a.stage_tx);
+            __syncwarp();
+            if (lane < 8 * NM1) {
+                const int arr = lane >> 3, gi = lane & 7;
+                const int e0 = 32 * s + 4 * gi;
+                const int32_t *src = arr == 0 ? mia : (arr == 1 ? mib : mic);
+                int r[4];
 #pragma unroll
-                for (int jj = 0; jj < TL; ++jj) z[jj] *= x;
-            } else {
-                const float sc = x * __ldg(a.Ua + (int64_t)mia[q] * a.Ka + ka);
-                ldg_vec<TL>(z, a.Ub + (int64_t)mib[q] * a.Kb + kb0);
-                ldg_vec<TV>(v, a.Uc + (int64_t)mic[q] * a.Kl + v0);
-#pragma unroll
-                for (int jj = 0; jj < TL; ++jj) z[jj] *= sc;
+                for (int q = 0; q < 4; ++q) r[q] = (e0 + q < len) ? src[e0 + q] : 0;
+                const CUtensorMap *tm = arr == 0 ? &tmA : (arr == 1 ? &tmB : &tmC);
+                const int sz = arr == 0 ? a.sa : (arr == 1 ? a.sb : a.sc);
+                const int off = arr == 0 ? 0 : (arr == 1 ? a.offb : a.offc);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                gather4(st + off + (size_t)gi * sz, tm, r[0], r[1], r[2], r[3], sbar + slot);
             }
         };
-        // accumulate the window-local elements q = q0, q0 + NG, ... < qe into y
-        auto accumulate = [&](int q0, int qe) {
-            int q = q0;
-            float z0[TL], w0[TV], z1[TL], w1[TV];
-            if (q < qe) load_nz(q, z0, w0);
-            while (q < qe) {
-                int qn = q + NG;
-                if (qn < qe) load_nz(qn, z1, w1);
+        for (int s = 0; s < nst && s < HY_NB; ++s) issue_stage(s);
+        int cur = -1;  // highest stage waited for in this window
+        // make stage s readable; release (re-issue) the stages before it
+        auto need_stage = [&](int s) {
+            while (cur < s) {
+                if (cur >= 0 && cur + HY_NB < nst) issue_stage(cur + HY_NB);
+                ++cur;
+                const int slot = (gst + cur) & (HY_NB - 1);
+                if (!mbar_wait(sbar + slot, (uint32_t)(((gst + cur) >> 2) & 1), a.err)) ok = false;
+            }
+        };
+        // y += contributions of window elements q in [qa, qb) owned by this lane's group
+        auto accumulate = [&](int qa, int qb) {
+            for (int k0 = (qa >> lg_ng) << lg_ng; k0 < qb; k0 += NG) {
+                need_stage(k0 >> 5);
+                const int q = k0 + g;
+                if (q >= qa && q < qb) {
+                    const int s = q >> 5, e = q & 31;
+                    const unsigned char *st = ring + (size_t)((gst + s) & (HY_NB - 1)) * a.stage_bytes;
+                    const float x = mval[q];
+                    float z[TL], v[TV];
+                    if (NM1 == 2) {
+                        const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
+                        const float *rb = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kl;
 #pragma unroll
-                for (int jj = 0; jj < TL; ++jj)
+                        for (int t = 0; t < TL / 4; ++t) {
+                            const float4 u = reinterpret_cast<const float4 *>(ra + l0)[t];
+                            z[4 * t] = u.x * x;
+                            z[4 * t + 1] = u.y * x;
+                            z[4 * t + 2] = u.z * x;
+                            z[4 * t + 3] = u.w * x;
+                        }
 #pragma unroll
-                    for (int kk = 0; kk < TV; ++kk) y[jj][kk] = fmaf(z0[jj], w0[kk], y[jj][kk]);
-                q = qn;
-                if (q >= qe) break;
-                qn = q + NG;
-                if (qn < qe) load_nz(qn, z0, w0);
+                        for (int t = 0; t < TV / 4; ++t) {
+                            const float4 u = reinterpret_cast<const float4 *>(rb + v0)[t];
+                            v[4 * t] = u.x;
+                            v[4 * t + 1] = u.y;
+                            v[4 * t + 2] = u.z;
+                            v[4 * t + 3] = u.w;
+                        }
+                    } else {
+                        const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
+                        const float *rb = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kb;
+                        const float *rc = reinterpret_cast<const float *>(st + a.offc + (e >> 2) * a.sc) + (e & 3) * a.Kl;
+                        const float sc = x * ra[ka];
 #pragma unroll
-                for (int jj = 0; jj < TL; ++jj)
+                        for (int t = 0; t < TL / 4; ++t) {
+                            const float4 u = reinterpret_cast<const float4 *>(rb + kb0)[t];
+                            z[4 * t] = u.x * sc;
+                            z[4 * t + 1] = u.y * sc;
+                            z[4 * t + 2] = u.z * sc;
+                            z[4 * t + 3] = u.w * sc;
+                        }
 #pragma unroll
-                    for (int kk = 0; kk < TV; ++kk) y[jj][kk] = fmaf(z1[jj], w1[kk], y[jj][kk]);
-                q = qn;
+                        for (int t = 0; t < TV / 4; ++t) {
+                            const float4 u = reinterpret_cast<const float4 *>(rc + v0)[t];
+                            v[4 * t] = u.x;
+                            v[4 * t + 1] = u.y;
+                            v[4 * t + 2] = u.z;
+                            v[4 * t + 3] = u.w;
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < TL; ++jj)
+#pragma unroll
+                        for (int kk = 0; kk < TV; ++kk) y[jj][kk] = fmaf(z[jj], v[kk], y[jj][kk]);
+                }
             }
         };
 
@@ -268,7 +308,7 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 const int64_t rs = a.lrp[j], re = a.lrp[j + 1];
                 const int64_t a1 = min(re, p1);
                 if (a1 <= pos) break;  // descriptors always advance; never spin on bad input
-                accumulate((int)(pos - p0) + g, (int)(a1 - p0));
+                accumulate((int)(pos - p0), (int)(a1 - p0));
                 const bool row_end = (a1 == re);
                 if (row_end || a1 == te) {
                     __syncwarp();
@@ -282,17 +322,7 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                     const int32_t r = a.lrow[j];
                     const bool full = (rs >= ts) && (re <= te);
                     const int slot = (j == a.item_aux[it]) ? 0 : 1;
-                    if (WA) {
-                        float *dst = full ? a.A + (int64_t)a.row_id[r] * a.Kn : a.apart + (it * 2 + slot) * a.Kn;
-                        const int rounds = (a.Kn + NG - 1) / NG;
-                        for (int t = 0; t < rounds; ++t) {
-                            const int kn = t * NG + g;
-                            float s = kn < a.Kn ? dot_tile(kn) : 0.f;
-                            for (int o = 1; o < lpn; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                            if (sub == 0 && kn < a.Kn) dst[kn] = s;
-                        }
-                    }
-                    if (WY && g == 0) store_tile(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (it * 2 + slot) * a.Pm);
+                    if (g == 0) store_tile(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (it * 2 + slot) * a.Pm);
                     zero_y();
                     if (row_end) ++j;
                 }
@@ -309,31 +339,31 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 const int64_t se = a.sbase[j + 1];
                 const int64_t a1 = min(se, p1);
                 if (a1 <= pos) break;
-                accumulate((int)(pos - p0) + g, (int)(a1 - p0));
+                accumulate((int)(pos - p0), (int)(a1 - p0));
                 if (a1 == se) {
                     __syncwarp();
                     const int32_t r = a.srow[j * NG + g];
-                    if (WA) {
-                        const int32_t row = r >= 0 ? a.row_id[r] : 0;
-                        for (int kn = 0; kn < a.Kn; ++kn) {
-                            float s = dot_tile(kn);
-                            for (int o = 1; o < lpn; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                            if (r >= 0 && sub == (kn & (lpn - 1))) a.A[(int64_t)row * a.Kn + kn] = s;
-                        }
-                    }
-                    if (WY && r >= 0) store_tile(a.Y + (int64_t)r * a.Pm);
+                    if (r >= 0) store_tile(a.Y + (int64_t)r * a.Pm);
                     zero_y();
                     ++j;
                 }
                 pos = a1;
             }
         }
+        // stages issued but not consumed (none: every stage of the window is waited for)
+        need_stage(nst - 1);
         __syncwarp();
+        gst += nst;
         it = nit;
         p0 = np0;
-        ++k;
+        ++mk;
+        if (!ok) break;
     }
-    if (!ok) mbar_wait(bar + ((k + 1) & 1), (uint32_t)(((k + 1) >> 1) & 1), nullptr);
+    if (!ok) {
+        // a staged copy never completed: bounded waits for this warp's other copies, then leave
+        mbar_wait(mbar + ((mk + 1) & 1), (uint32_t)(((mk + 1) >> 1) & 1), nullptr);
+        for (int q = 0; q < HY_NB; ++q) mbar_wait(sbar + q, (uint32_t)(((gst + q) >> 2) & 1), nullptr);
+    }
 }
 
 // A and Y rows of the long rows cut by task boundaries: sum of the pieces in task order.
@@ -358,81 +388,175 @@ __global__ void __launch_bounds__(256) k_span_fix(const int32_t *span, const int
         }
 }
 
-// CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) * Y[r][e] over a fixed
-// row range per CTA.  Thread t owns columns e = t + 256*s (s < ES) and KC values
-// of kn per round.
-template <int ES, int KC>
-__global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
-                                                     int Kn, int Pm, int64_t rpb, float *cpart) {
-    constexpr int RB = 64;
-    __shared__ float Us[RB * KC];
-    const int64_t r0 = (int64_t)blockIdx.x * rpb;
-    const int64_t r1 = min(r0 + rpb, R);
-    const int KnPm = Kn * Pm;
-    for (int kc = 0; kc < Kn; kc += KC) {
-        float acc[ES][KC];
+// A(row_id[r], :) = G_(n) y_r for every stored row (the TTMcTC output, Eq.
+// ttmctc, from the rows of Y_(n)).  Register tiles of 4 rows x 4 values of k_n
+// per thread; Y and G_(n) are staged through shared memory in chunks of EC
+// columns.  Rows of A without nonzeros stay as cleared by the caller.
+__global__ void __launch_bounds__(256) k_a_from_y(const float *Y, const float *Gn, const int32_t *row_id, int64_t R,
+                                                  int Kn, int Knp, int Pm, int RT, float *A) {
+    extern __shared__ __align__(16) float dsm[];
+    const int EC = Pm < 32 ? Pm : 32;
+    float *YT = dsm;                    // [EC][RT + 4]
+    float *GT = dsm + EC * (RT + 4);    // [EC][Knp]
+    const int nkq = Knp >> 2;
+    const int t = threadIdx.x;
+    const int kq = t % nkq, rq = t / nkq;
+    const bool active = rq < (RT >> 2);
+    for (int64_t r0 = (int64_t)blockIdx.x * RT; r0 < R; r0 += (int64_t)gridDim.x * RT) {
+        float acc[4][4];
 #pragma unroll
-        for (int s = 0; s < ES; ++s)
+        for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int q = 0; q < KC; ++q) acc[s][q] = 0.f;
-        for (int64_t rb = r0; rb < r1; rb += RB) {
-            const int nr = (int)min((int64_t)RB, r1 - rb);
+            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+        for (int e0 = 0; e0 < Pm; e0 += EC) {
             __syncthreads();
-            for (int t = threadIdx.x; t < nr * KC; t += blockDim.x) {
-                const int rr = t / KC, q = t - rr * KC;
-                Us[t] = (kc + q < Kn) ? Un[(int64_t)row_id[rb + rr] * Kn + kc + q] : 0.f;
+            const int nq = EC >> 2;
+            for (int idx = t; idx < RT * nq; idx += blockDim.x) {
+                const int rr = idx / nq, c4 = idx - rr * nq;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (r0 + rr < R) v = *reinterpret_cast<const float4 *>(Y + (r0 + rr) * Pm + e0 + 4 * c4);
+                YT[(4 * c4 + 0) * (RT + 4) + rr] = v.x;
+                YT[(4 * c4 + 1) * (RT + 4) + rr] = v.y;
+                YT[(4 * c4 + 2) * (RT + 4) + rr] = v.z;
+                YT[(4 * c4 + 3) * (RT + 4) + rr] = v.w;
+            }
+            for (int idx = t; idx < EC * Knp; idx += blockDim.x) {
+                const int e = idx / Knp, kn = idx - e * Knp;
+                GT[idx] = kn < Kn ? Gn[(size_t)kn * Pm + e0 + e] : 0.f;
             }
             __syncthreads();
-            for (int rr = 0; rr < nr; ++rr) {
-                const float *yr = Y + (rb + rr) * Pm;
+            if (active) {
+                for (int e = 0; e < EC; ++e) {
+                    const float4 y4 = *reinterpret_cast<const float4 *>(YT + e * (RT + 4) + 4 * rq);
+                    const float4 g4 = *reinterpret_cast<const float4 *>(GT + e * Knp + 4 * kq);
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
 #pragma unroll
-                for (int s = 0; s < ES; ++s) {
-                    const int e = threadIdx.x + 256 * s;
-                    const float yv = e < Pm ? yr[e] : 0.f;
+                    for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int q = 0; q < KC; ++q) acc[s][q] = fmaf(Us[rr * KC + q], yv, acc[s][q]);
+                        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(yv[i], gv[k], acc[i][k]);
                 }
             }
         }
+        if (active) {
 #pragma unroll
-        for (int s = 0; s < ES; ++s) {
-            const int e = threadIdx.x + 256 * s;
-            if (e >= Pm) continue;
+            for (int i = 0; i < 4; ++i) {
+                const int64_t r = r0 + 4 * rq + i;
+                if (r >= R) continue;
+                float *arow = A + (int64_t)row_id[r] * Kn;
 #pragma unroll
-            for (int q = 0; q < KC; ++q)
-                if (kc + q < Kn) cpart[(size_t)blockIdx.x * KnPm + (size_t)(kc + q) * Pm + e] = acc[s][q];
+                for (int k = 0; k < 4; ++k)
+                    if (4 * kq + k < Kn) arow[4 * kq + k] = acc[i][k];
+            }
+        }
+    }
+}
+
+// CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) * Y[r][e] over a
+// fixed row range per CTA (Sec. 2.2: G = U_n^T Y_(n)).  Each thread owns 4 x 4
+// (kn, e) tiles; U rows are staged in shared memory 64 at a time.
+__global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
+                                                     int Kn, int Knp, int Pm, int64_t rpb, float *cpart) {
+    constexpr int RB = 64;
+    extern __shared__ __align__(16) float Us[];  // [RB][Knp]
+    const int64_t r0 = (int64_t)blockIdx.x * rpb;
+    const int64_t r1 = min(r0 + rpb, R);
+    const int KnPm = Kn * Pm;
+    const int nkq = Knp >> 2, neq = Pm >> 2;
+    const int nasg = nkq * neq;
+    for (int base = 0; base < nasg; base += blockDim.x) {
+        const int asg = base + threadIdx.x;
+        const bool active = asg < nasg;
+        const int kq = active ? asg / neq : 0;
+        const int eq = active ? asg - kq * neq : 0;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
+        for (int64_t rb = r0; rb < r1; rb += RB) {
+            const int nr = (int)min((int64_t)RB, r1 - rb);
+            __syncthreads();
+            for (int t = threadIdx.x; t < nr * Knp; t += blockDim.x) {
+                const int rr = t / Knp, q = t - rr * Knp;
+                Us[t] = q < Kn ? Un[(int64_t)row_id[rb + rr] * Kn + q] : 0.f;
+            }
+            __syncthreads();
+            if (active) {
+                for (int rr = 0; rr < nr; ++rr) {
+                    const float4 u4 = *reinterpret_cast<const float4 *>(Us + rr * Knp + 4 * kq);
+                    const float4 y4 = __ldg(reinterpret_cast<const float4 *>(Y + (rb + rr) * Pm) + eq);
+                    const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(uv[i], yv[k], acc[i][k]);
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int kn = 4 * kq + i;
+                if (kn >= Kn) continue;
+                float4 *dst = reinterpret_cast<float4 *>(cpart + (size_t)blockIdx.x * KnPm + (size_t)kn * Pm) + eq;
+                *dst = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+            }
         }
     }
 }
 
 struct HybLaunch {
     size_t smem = 0;
-    int gs_off = 0, w_off = 0, w_stride = 0;
+    int bar_off = 0, gs_off = 0, w_off = 0, w_stride = 0, meta_bytes = 0, ring_off = 0, stage_bytes = 0;
+    int stage_tx = 0, sa = 0, sb = 0, sc = 0, offb = 0, offc = 0;
 };
 
-HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p, bool wa) {
+inline int al128(int x) { return (x + 127) & ~127; }
+
+HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p) {
     HybLaunch L;
-    const int KnPm = c->K[n] * p.Pm;
     const int narr = p.nm1 + 1;
-    L.gs_off = 32;
-    L.w_off = L.gs_off + (wa ? ((KnPm + 31) & ~31) : 0);
-    L.w_stride = (2 * narr * HY_WB + 31) & ~31;
-    L.smem = (size_t)(L.w_off + HY_WARPS * L.w_stride) * sizeof(float);
+    // ranks of the gathered rows: (Ua, Ub[, Uc]) = other modes in ascending order
+    int K3[3] = {0, 0, 0}, j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) K3[j++] = c->K[m];
+    L.sa = std::max(16 * K3[0], 128);
+    L.sb = std::max(16 * K3[1], 128);
+    L.sc = p.nm1 == 3 ? std::max(16 * K3[2], 128) : 0;
+    L.offb = 8 * L.sa;
+    L.offc = L.offb + 8 * L.sb;
+    L.stage_bytes = al128(8 * (L.sa + L.sb + L.sc));
+    L.stage_tx = 128 * (K3[0] + K3[1] + (p.nm1 == 3 ? K3[2] : 0));
+    L.meta_bytes = HY_WB * 4;
+    L.bar_off = 0;
+    L.gs_off = al128(HY_WARPS * (2 + HY_NB) * 8);
+    L.w_off = L.gs_off;
+    L.ring_off = al128(2 * narr * L.meta_bytes);
+    L.w_stride = al128(L.ring_off + HY_NB * L.stage_bytes);
+    L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
     return L;
 }
 
-template <int NM1, bool WA, bool WY>
-hoqri_status launch_hyb_nm1(hoqri_ctx *c, const FastTile &p, HybArgs &a, const HybLaunch &L) {
+template <int NM1>
+hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, const HybLaunch &L) {
+    int oth[3] = {0, 0, 0}, j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) oth[j++] = m;
+    const CUtensorMap &tA = c->tmap[oth[0]];
+    const CUtensorMap &tB = c->tmap[oth[1]];
+    const CUtensorMap &tC = c->tmap[NM1 == 3 ? oth[2] : oth[0]];
 #define HQ_HYB(TLV, TVV)                                                                                    \
     if (p.TL == TLV && p.TV == TVV) {                                                                       \
-        auto kern = k_hyb<NM1, TLV, TVV, WA, WY>;                                                           \
+        auto kern = k_hyb<NM1, TLV, TVV>;                                                           \
         HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));     \
         int per_sm = 0;                                                                                     \
         HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HY_WARPS * 32, L.smem));      \
         per_sm = std::max(1, std::min(per_sm, 4));                                                          \
         const int grid = (int)std::max<int64_t>(                                                            \
             1, std::min<int64_t>((int64_t)c->num_sms * per_sm, ceil_div(std::max<int64_t>(a.nitem, 1), HY_WARPS))); \
-        kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                                \
+        kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(tA, tB, tC, a);                                    \
         c->nlaunch++;                                                                                       \
         HQ_CUDA(cudaGetLastError());                                                                        \
         return HOQRI_OK;                                                                                    \
@@ -448,15 +572,47 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, const FastTile &p, HybArgs &a, const H
 
 }  // namespace
 
-bool hyb_mode(const hoqri_ctx *c, int n) { return c->ms[n].hyb && c->Y != nullptr; }
+bool hyb_mode(const hoqri_ctx *c, int n) { return c->ms[n].hyb && c->Y != nullptr && c->tmap_ok; }
 
-// The pass over mode n's hybrid stream.  Gn (unfolded core [Kn][Pm], device)
-// and A_out are used when A_out != nullptr; Y is written when write_y.
-hoqri_status hyb_pass(hoqri_ctx *c, int n, const float *Gn, float *A_out, bool write_y) {
+// One 2-D tensor map per factor U_m (I_m x K_m FP32, row-major), box = one full
+// row, for the gather4 loads of the hybrid pass.  The factors keep their device
+// buffers for the life of the context, so the maps are encoded once.
+hoqri_status encode_factor_maps(hoqri_ctx *c) {
+    c->tmap_ok = false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return HOQRI_OK;  // no tensor maps: the modes fall back to the two-pass kernels
+    }
+    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    for (int m = 0; m < c->N; ++m) {
+        if (c->prec != HOQRI_FP32 || c->K[m] % 4 != 0) continue;
+        const cuuint64_t gdim[2] = {(cuuint64_t)c->K[m], (cuuint64_t)c->dims[m]};
+        const cuuint64_t gstride[1] = {(cuuint64_t)c->K[m] * sizeof(float)};
+        const cuuint32_t box[2] = {(cuuint32_t)c->K[m], 1};
+        const cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(&c->tmap[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->U[m], gdim, gstride, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("cuTensorMapEncodeTiled failed for a factor");
+            return HOQRI_ERR_CUDA;
+        }
+    }
+    c->tmap_ok = true;
+    return HOQRI_OK;
+}
+
+// The pass over mode n's hybrid stream: writes every row y_r of Y_(n) into the
+// dense R_n x P_{-n} buffer c->Y (rows cut by task boundaries are completed by
+// k_span_fix).
+hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     const ModeStore &M = c->ms[n];
     FastTile p;
-    if (!fast_tile(c, n, &p)) {
-        set_error("hybrid pass: mode has no register-tile plan");
+    if (!fast_tile(c, n, &p) || !c->tmap_ok) {
+        set_error("hybrid pass: mode has no register-tile plan or tensor maps");
         return HOQRI_ERR_UNSUPPORTED;
     }
     HybArgs a{};
@@ -467,16 +623,9 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n, const float *Gn, float *A_out, bool w
     a.Kb = p.Kb;
     a.GV = p.GV;
     a.lpn = p.lpn;
-    const float *Uo[3] = {nullptr, nullptr, nullptr};
-    int j = 0;
-    for (int m = 0; m < c->N; ++m)
-        if (m != n) Uo[j++] = (const float *)c->U[m];
     a.ia = M.hidx[0];
     a.ib = M.hidx[1];
     a.ic = p.nm1 == 3 ? M.hidx[2] : nullptr;
-    a.Ua = Uo[0];
-    a.Ub = Uo[1];
-    a.Uc = Uo[2];
     a.vals = (const float *)M.hvals;
     a.row_id = M.row_id;
     a.lrp = M.lrp;
@@ -488,70 +637,77 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n, const float *Gn, float *A_out, bool w
     a.item_aux = M.item_aux;
     a.nitem = M.nitem;
     a.nitem_long = M.nitem_long;
-    const bool wa = A_out != nullptr;
-    HybLaunch L = hyb_launch(c, n, p, wa);
-    a.warps = HY_WARPS;
+    HybLaunch L = hyb_launch(c, n, p);
+    a.bar_off = L.bar_off;
     a.gs_off = L.gs_off;
     a.w_off = L.w_off;
     a.w_stride = L.w_stride;
-    a.Gn = Gn;
-    a.A = A_out;
+    a.meta_bytes = L.meta_bytes;
+    a.ring_off = L.ring_off;
+    a.stage_bytes = L.stage_bytes;
+    a.stage_tx = L.stage_tx;
+    a.sa = L.sa;
+    a.sb = L.sb;
+    a.sc = L.sc;
+    a.offb = L.offb;
+    a.offc = L.offc;
     a.Y = c->Y;
-    a.apart = (float *)c->a_part;
     a.ypart = c->ypart;
     a.err = c->dflag + 2;
-    if (wa) HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * a.Kn * sizeof(float), c->stream));
-    hoqri_status s;
-    if (p.nm1 == 2) {
-        if (wa && write_y) s = launch_hyb_nm1<2, true, true>(c, p, a, L);
-        else if (wa) s = launch_hyb_nm1<2, true, false>(c, p, a, L);
-        else s = launch_hyb_nm1<2, false, true>(c, p, a, L);
-    } else {
-        if (wa && write_y) s = launch_hyb_nm1<3, true, true>(c, p, a, L);
-        else if (wa) s = launch_hyb_nm1<3, true, false>(c, p, a, L);
-        else s = launch_hyb_nm1<3, false, true>(c, p, a, L);
-    }
-    HQ_TRY(s);
+    HQ_TRY(p.nm1 == 2 ? launch_hyb_nm1<2>(c, n, p, a, L) : launch_hyb_nm1<3>(c, n, p, a, L));
     if (M.nspan > 0) {
-        k_span_fix<<<(unsigned)M.nspan, 256, 0, c->stream>>>(M.span, M.lrow, M.row_id, M.item_aux,
-                                                              (const float *)c->a_part, c->ypart, a.Kn, a.Pm,
-                                                              wa ? A_out : nullptr, write_y ? c->Y : nullptr);
+        k_span_fix<<<(unsigned)M.nspan, 256, 0, c->stream>>>(M.span, M.lrow, M.row_id, M.item_aux, nullptr,
+                                                              c->ypart, a.Kn, a.Pm, nullptr, c->Y);
         c->nlaunch++;
     }
     HQ_CUDA(cudaGetLastError());
     return HOQRI_OK;
 }
 
-// G_(n) = U_n^T Y_(n) (Y written by the last hyb_pass of mode n) into CTA
-// partials; returns the number of CTAs (the partial count).
+// A_n = Y_(n) G_(n)^T from the stored rows (Gn: G_(n) as [Kn][Pm] on the device).
+hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
+    const ModeStore &M = c->ms[n];
+    const int Kn = c->K[n];
+    const int Pm = (int)(c->P / Kn);
+    const int Knp = (Kn + 3) & ~3;
+    const int RT = std::min(256, 4 * (256 / (Knp / 4)));
+    const int EC = Pm < 32 ? Pm : 32;
+    const size_t smem = ((size_t)EC * (RT + 4) + (size_t)EC * Knp) * sizeof(float);
+    HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * Kn * sizeof(float), c->stream));
+    if (M.R > 0) {
+        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, RT), (int64_t)c->num_sms * 4));
+        k_a_from_y<<<grid, 256, smem, c->stream>>>(c->Y, Gn, M.row_id, M.R, Kn, Knp, Pm, RT, A_out);
+        c->nlaunch++;
+    }
+    HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+// G_(n) = U_n^T Y_(n) (Y from the last hyb_pass of mode n) into CTA partials;
+// *nblk receives the number of partials.
 hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
     const ModeStore &M = c->ms[n];
     const int Kn = c->K[n];
     const int Pm = (int)(c->P / Kn);
+    const int Knp = (Kn + 3) & ~3;
     const int64_t R = M.R;
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
-                                                          (int64_t)c->num_sms * 2));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
+                                                                (int64_t)c->num_sms * 2));
     const int64_t rpb = ceil_div(std::max<int64_t>(R, 1), grid);
-    float *cp = (float *)c->core_part;
-    const float *Un = (const float *)c->U[n];
-    if (Pm <= 256)
-        k_core_from_y<1, 16><<<grid, 256, 0, c->stream>>>(c->Y, Un, M.row_id, R, Kn, Pm, rpb, cp);
-    else if (Pm <= 512)
-        k_core_from_y<2, 16><<<grid, 256, 0, c->stream>>>(c->Y, Un, M.row_id, R, Kn, Pm, rpb, cp);
-    else if (Pm <= 1024)
-        k_core_from_y<4, 8><<<grid, 256, 0, c->stream>>>(c->Y, Un, M.row_id, R, Kn, Pm, rpb, cp);
-    else
-        k_core_from_y<8, 4><<<grid, 256, 0, c->stream>>>(c->Y, Un, M.row_id, R, Kn, Pm, rpb, cp);
+    const size_t smem = (size_t)64 * Knp * sizeof(float);
+    k_core_from_y<<<grid, 256, smem, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Kn, Knp, Pm, rpb,
+                                                  (float *)c->core_part);
     c->nlaunch++;
     HQ_CUDA(cudaGetLastError());
     *nblk = grid;
     return HOQRI_OK;
 }
 
-size_t hyb_smem_need(const hoqri_ctx *c, int n, bool wa) {
+size_t hyb_smem_need(const hoqri_ctx *c, int n) {
     FastTile p;
     if (!fast_tile(c, n, &p)) return (size_t)-1;
-    return hyb_launch(c, n, p, wa).smem;
+    return hyb_launch(c, n, p).smem;
 }
 
 size_t hyb_smem_cap() { return HY_SMEM_CAP; }

@@ -1,7 +1,9 @@
 // Internal declarations shared by the translation units of libhoqri.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 #include <stdint.h>
 
 #include <string>
@@ -119,6 +121,8 @@ struct hoqri_ctx {
     double *qr_small = nullptr;         // K x K FP64 workspace (Rinv) and norms
     double *qr_work = nullptr;          // Householder fallback workspace (max I*K doubles)
     double *gnorm_part = nullptr;       // block partials of ||G||^2
+    CUtensorMap tmap[HOQRI_MAXN];       // 2-D maps of the factors for TMA gathers
+    bool tmap_ok = false;
     float *Y = nullptr;                 // rows y_i of Y_(n) for the modes using the hybrid kernels
     int64_t Y_bytes = 0;
     float *ypart = nullptr;             // [nitem_long][2][P_{-n}] pieces of rows cut by long tasks
@@ -169,9 +173,11 @@ hoqri_status unfold_core(hoqri_ctx *c, int n, const void *G, void *Gn);
 
 // one-stream FP32 passes on the hybrid layout (hybrid.cu)
 bool hyb_mode(const hoqri_ctx *c, int n);
-hoqri_status hyb_pass(hoqri_ctx *c, int n, const float *Gn, float *A_out, bool write_y);
+hoqri_status encode_factor_maps(hoqri_ctx *c);
+hoqri_status hyb_pass(hoqri_ctx *c, int n);
+hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out);
 hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk);
-size_t hyb_smem_need(const hoqri_ctx *c, int n, bool wa);
+size_t hyb_smem_need(const hoqri_ctx *c, int n);
 size_t hyb_smem_cap();
 hoqri_status passes_init(hoqri_ctx *c);
 hoqri_status core_pass(hoqri_ctx *c, int n, void *G_out, double *normG2_slot);

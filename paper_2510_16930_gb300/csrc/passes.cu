@@ -538,25 +538,32 @@ __device__ __forceinline__ int64_t rowmajor_of(const CoreMap &m, int p) {
 
 // G (row-major) = sum over CTAs of the [Kn][Pm] partials, in CTA order; block
 // partial sums of ||G||^2.
+// Each block owns 32 consecutive entries p; its 8 warps sum the partials
+// b = w, w + 8, ... of those entries (lane = entry), then warp 0 adds the 8
+// warp sums in warp order.  The order of every sum is fixed.
 template <typename T>
-__global__ void k_core_reduce(const T *cpart, int nblk, CoreMap m, T *G, double *gpart) {
-    __shared__ double sh[RED_TPB];
+__global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nblk, CoreMap m, T *G, double *gpart) {
+    __shared__ double sh[RED_TPB / 32][33];
     const int P = m.Kn * m.Pm;
-    double sq = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += (double)cpart[(size_t)b * P + p];
-        const T v = (T)s;
-        G[rowmajor_of(m, p)] = v;
-        sq += (double)v * (double)v;
-    }
-    sh[threadIdx.x] = sq;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = RED_TPB / 32;
+    const int p = blockIdx.x * 32 + lane;
+    double s = 0.0;
+    if (p < P)
+        for (int b = w; b < nblk; b += nw) s += (double)cpart[(size_t)b * P + p];
+    sh[w][lane] = s;
     __syncthreads();
-    for (int w = RED_TPB / 2; w > 0; w >>= 1) {
-        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
+    if (w == 0) {
+        double t = 0.0;
+        for (int q = 0; q < nw; ++q) t += sh[q][lane];
+        double sq = 0.0;
+        if (p < P) {
+            const T v = (T)t;
+            G[rowmajor_of(m, p)] = v;
+            sq = (double)v * (double)v;
+        }
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) gpart[blockIdx.x] = sq;
     }
-    if (threadIdx.x == 0) gpart[blockIdx.x] = sh[0];
 }
 
 __global__ void k_sum_into(const double *part, int n, double *out, double *out2) {
@@ -825,7 +832,7 @@ hoqri_status core_pass_t(hoqri_ctx *c, int n, void *G_out, double *normG2_slot) 
         HQ_TRY((launch_generic<T, true>(c, a, grid, smem)));
     }
     CoreMap m = core_map(c, n);
-    const int rb = std::max(1, std::min(64, (KnPm + RED_TPB - 1) / RED_TPB));
+    const int rb = (KnPm + 31) / 32;
     k_core_reduce<T><<<rb, RED_TPB, 0, c->stream>>>((const T *)c->core_part, grid, m, (T *)G_out, c->gnorm_part);
     k_sum_into<<<1, 32, 0, c->stream>>>(c->gnorm_part, rb, c->dnorm + 1, normG2_slot);
     c->nlaunch += 2;
@@ -884,7 +891,7 @@ bool fast_tile(const hoqri_ctx *c, int n, FastTile *out) {
 hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *normG2_slot) {
     CoreMap m = core_map(c, n);
     const int KnPm = m.Kn * m.Pm;
-    const int rb = std::max(1, std::min(64, (KnPm + RED_TPB - 1) / RED_TPB));
+    const int rb = (KnPm + 31) / 32;
     if (c->prec == HOQRI_FP64)
         k_core_reduce<double><<<rb, RED_TPB, 0, c->stream>>>((const double *)c->core_part, nblk, m, (double *)G_out,
                                                               c->gnorm_part);
@@ -952,6 +959,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
         if ((int64_t)GEN_WARPS * wst * (int64_t)c->rsize > (int64_t)SMEM_CAP)
             ab = std::max(ab, (int64_t)c->core_grid * GEN_WARPS * c->P * (int64_t)c->rsize);
     }
+    HQ_TRY(encode_factor_maps(c));
     // hybrid layout + dense Y for the FP32 modes with a register-tile plan
     int64_t ybytes = 0, ypb = 0;
     const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 32)));
@@ -959,7 +967,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
     for (int n = 0; n < c->N; ++n) {
         FastTile p;
         if (!fast_tile(c, n, &p) || c->opt.one_stream == 2) continue;
-        if (hyb_smem_need(c, n, true) > hyb_smem_cap()) continue;
+        if (hyb_smem_need(c, n) > hyb_smem_cap()) continue;
         HQ_TRY(build_hybrid(c, n, 256, T32, 32 / p.lpn));
         const ModeStore &M = c->ms[n];
         ab = std::max<int64_t>(ab, std::max<int64_t>(M.nitem_long, 1) * 2 * c->K[n] * (int64_t)c->rsize);
@@ -975,7 +983,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
         HQ_TRY(dalloc(c, (void **)&c->ypart, ypb));
         c->ypart_bytes = ypb;
     }
-    HQ_TRY(dalloc(c, (void **)&c->gnorm_part, 64 * sizeof(double)));
+    HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((c->P + 31) / 32 + 1) * sizeof(double)));
     return HOQRI_OK;
 }
 

@@ -83,16 +83,21 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
     __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
     __shared__ int broke;
     const int npairs = K * (K + 1) / 2;
-    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        int rem = p, i = 0;
-        while (rem >= K - i) {
-            rem -= K - i;
-            ++i;
-        }
-        int j = i + rem;
+    // W(i, j) = sum of the block partials: one warp per pair, lanes stride the
+    // blocks, then a fixed butterfly (same order every run)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int p = wid; p < npairs; p += nwarp) {
         double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * npairs + p];
-        W[i * K + j] = s;
+        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * npairs + p];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) {
+            int rem = p, i = 0;
+            while (rem >= K - i) {
+                rem -= K - i;
+                ++i;
+            }
+            W[i * K + i + rem] = s;
+        }
     }
     if (threadIdx.x == 0) broke = 0;
     __syncthreads();
@@ -135,41 +140,60 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
     }
 }
 
-// out(r, c) = sum_{i <= c} A(r, i) Rinv(i, c); one thread per output element (out != A)
-template <typename T>
-__global__ void __launch_bounds__(256) k_apply(const T *A, int64_t I, int K, const double *Rinv, T *out,
-                                               const int32_t *flag) {
+// out(r, :) = A(r, :) Rinv (Rinv upper triangular), one thread per row; the
+// thread reads its whole row before writing, so out may alias A.  FP32 rows
+// are multiplied in FP32 (the factor is stored in FP32), FP64 rows in FP64.
+template <typename T, int KC>
+__global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const double *Rinv, T *out,
+                                                    const int32_t *flag) {
     if (*flag != 0) return;
-    __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
+    __shared__ T Rs[KC * KC];
+    for (int t = threadIdx.x; t < KC * KC; t += blockDim.x) Rs[t] = (T)Rinv[t];
     __syncthreads();
-    const int64_t total = I * K;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t r = t / K;
-        const int c = (int)(t - r * K);
-        const T *a = A + r * K;
-        double s = 0.0;
-        for (int i = 0; i <= c; ++i) s += (double)a[i] * Rs[i * K + c];
-        out[t] = (T)s;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
+        T a[KC], o[KC];
+#pragma unroll
+        for (int i = 0; i < KC; ++i) a[i] = A[r * KC + i];
+#pragma unroll
+        for (int c = 0; c < KC; ++c) {
+            T s = T(0);
+#pragma unroll
+            for (int i = 0; i <= c; ++i) s = fma(a[i], Rs[i * KC + c], s);
+            o[c] = s;
+        }
+#pragma unroll
+        for (int c = 0; c < KC; ++c) out[r * KC + c] = o[c];
     }
 }
 
-// in-place variant needs the whole row read before it is overwritten
+// any K <= 64: one thread per row, row kept in local memory
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply_inplace(T *A, int64_t I, int K, const double *Rinv, const int32_t *flag) {
+__global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, int K, const double *Rinv, T *out,
+                                                        const int32_t *flag) {
     if (*flag != 0) return;
     __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
     __syncthreads();
-    // one thread per row: reads the row into registers, then writes it
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
         double a[HOQRI_MAXK];
         for (int i = 0; i < K; ++i) a[i] = (double)A[r * K + i];
         for (int c = 0; c < K; ++c) {
             double s = 0.0;
             for (int i = 0; i <= c; ++i) s += a[i] * Rs[i * K + c];
-            A[r * K + c] = (T)s;
+            out[r * K + c] = (T)s;
         }
+    }
+}
+
+template <typename T>
+void launch_apply(hoqri_ctx *c, const T *A, int64_t I, int K, const double *Rinv, T *out, int grid) {
+    cudaStream_t st = c->stream;
+    switch (K) {
+        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
+        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
+        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
+        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
+        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, c->dflag); break;
     }
 }
 
@@ -303,7 +327,6 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     const int64_t rpb = ceil_div(I, nb);
     const int npairs = K * (K + 1) / 2;
     double *Rinv = c->qr_small;
-    const int apply_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I * K, 256), (int64_t)c->num_sms * 8));
     const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
     if (c->opt.qr_kind == 1) {
         int32_t one = 1;
@@ -315,10 +338,7 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
         k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(A, I, K, rpb, c->qr_part, c->dflag);
         k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, Rinv, c->dflag);
         k_householder<T><<<1, HH_TPB, 0, st>>>(A, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
-        if (pass == 0)
-            k_apply_inplace<T><<<apply_rows_grid, 256, 0, st>>>(A, I, K, Rinv, c->dflag);
-        else
-            k_apply<T><<<apply_grid, 256, 0, st>>>(A, I, K, Rinv, U, c->dflag);
+        launch_apply<T>(c, A, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
         c->nlaunch += 4;
     }
     (void)npairs;
