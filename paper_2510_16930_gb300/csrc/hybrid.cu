@@ -87,6 +87,7 @@ struct HybArgs {
     const int64_t *item_s, *item_e;
     const int32_t *item_aux;
     int64_t nitem, nitem_long;
+    int64_t ipw, nrange;                   // items per warp range, number of ranges
     int bar_off, gs_off, w_off, w_stride;  // shared memory layout (bytes)
     int meta_bytes;                        // one staged array of a window (HY_WB floats)
     int ring_off, stage_bytes;             // gathered factor rows: NB stages per warp
@@ -161,12 +162,13 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
         }
     };
 
-    float y[TL][TV];
+    // y tile as column pairs: y2[j][k] holds columns (2k, 2k+1) of tile row j
+    float2 y2[TL][TV / 2];
     auto zero_y = [&]() {
 #pragma unroll
         for (int j = 0; j < TL; ++j)
 #pragma unroll
-            for (int k = 0; k < TV; ++k) y[j][k] = 0.f;
+            for (int k = 0; k < TV / 2; ++k) y2[j][k] = make_float2(0.f, 0.f);
     };
     auto store_tile = [&](float *dst) {
 #pragma unroll
@@ -174,23 +176,39 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
             float4 *p = reinterpret_cast<float4 *>(dst + (size_t)(l0 + j) * a.Kl + v0);
 #pragma unroll
             for (int k4 = 0; k4 < TV / 4; ++k4)
-                p[k4] = make_float4(y[j][4 * k4], y[j][4 * k4 + 1], y[j][4 * k4 + 2], y[j][4 * k4 + 3]);
+                p[k4] = make_float4(y2[j][2 * k4].x, y2[j][2 * k4].y, y2[j][2 * k4 + 1].x, y2[j][2 * k4 + 1].y);
         }
     };
     bool ok = true;
     int mk = 0;         // meta windows consumed by this warp
     int gst = 0;        // factor-row stages consumed by this warp (wraps harmlessly)
-    int64_t it = gw;
+    // work of this warp: a contiguous range of long-row items (rows carry across
+    // items inside the range), then every nw-th slice item
+    const int64_t rg = gw;
+    const int64_t r0 = rg * a.ipw;
+    const int64_t r1 = rg < a.nrange ? min(r0 + a.ipw, a.nitem_long) : r0;
+    auto next_item = [&](int64_t cur) -> int64_t {
+        if (cur < a.nitem_long) {
+            if (cur + 1 < r1) return cur + 1;
+            return a.nitem_long + gw;
+        }
+        return cur + nw;
+    };
+    const int64_t lfirst = (r0 < r1) ? a.item_aux[r0] : -1;
+    const int64_t lbeg = (r0 < r1) ? a.item_s[r0] : 0;
+    const int64_t lend = (r0 < r1) ? a.item_e[r1 - 1] : 0;
+    int64_t it = (r0 < r1) ? r0 : a.nitem_long + gw;
     int64_t p0 = it < a.nitem ? a.item_s[it] : 0;
     if (it < a.nitem) issue_meta(p0, min(p0 + (int64_t)HY_W, a.item_e[it]), 0);
     int64_t j = 0;
+    bool carry = false;  // a long row continues from the previous item of this range
     while (it < a.nitem) {
         const int mbuf = mk & 1;
         const int64_t ts = a.item_s[it], te = a.item_e[it];
         const int64_t p1 = min(p0 + (int64_t)HY_W, te);
         int64_t nit = it, np0 = p0 + HY_W;
         if (np0 >= te) {
-            nit = it + nw;
+            nit = next_item(it);
             np0 = nit < a.nitem ? a.item_s[nit] : 0;
         }
         if (nit < a.nitem) issue_meta(np0, min(np0 + (int64_t)HY_W, a.item_e[nit]), mbuf ^ 1);
@@ -238,91 +256,122 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
                 if (!mbar_wait(sbar + slot, (uint32_t)(((gst + cur) >> 2) & 1), a.err)) ok = false;
             }
         };
-        // y += contributions of window elements q in [qa, qb) owned by this lane's group
-        auto accumulate = [&](int qa, int qb) {
-            for (int k0 = (qa >> lg_ng) << lg_ng; k0 < qb; k0 += NG) {
-                need_stage(k0 >> 5);
-                const int q = k0 + g;
-                if (q >= qa && q < qb) {
-                    const int s = q >> 5, e = q & 31;
-                    const unsigned char *st = ring + (size_t)((gst + s) & (HY_NB - 1)) * a.stage_bytes;
-                    const float x = mval[q];
-                    float z[TL], v[TV];
-                    if (NM1 == 2) {
-                        const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
-                        const float *rb = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kl;
+        // operands of window element q (its stage has landed): z = x * (Kronecker
+        // prefix rows), v = last other mode's row, both restricted to the lane's tile
+        auto load_elem = [&](const unsigned char *st, int q, float (&z)[TL], float2 (&v)[TV / 2]) {
+            const int e = q & 31;
+            float x = mval[q];
+            const float *rz;
+            const float4 *rv;
+            if (NM1 == 2) {
+                rz = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka + l0;
+                rv = reinterpret_cast<const float4 *>(
+                    reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kl + v0);
+            } else {
+                const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
+                x *= ra[ka];
+                rz = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kb + kb0;
+                rv = reinterpret_cast<const float4 *>(
+                    reinterpret_cast<const float *>(st + a.offc + (e >> 2) * a.sc) + (e & 3) * a.Kl + v0);
+            }
 #pragma unroll
-                        for (int t = 0; t < TL / 4; ++t) {
-                            const float4 u = reinterpret_cast<const float4 *>(ra + l0)[t];
-                            z[4 * t] = u.x * x;
-                            z[4 * t + 1] = u.y * x;
-                            z[4 * t + 2] = u.z * x;
-                            z[4 * t + 3] = u.w * x;
+            for (int t = 0; t < TL / 4; ++t) {
+                const float4 u = reinterpret_cast<const float4 *>(rz)[t];
+                z[4 * t] = u.x;
+                z[4 * t + 1] = u.y;
+                z[4 * t + 2] = u.z;
+                z[4 * t + 3] = u.w;
+            }
+            const float2 xx = make_float2(x, x);
+#pragma unroll
+            for (int t = 0; t < TV / 4; ++t) {
+                const float4 u = rv[t];
+                v[2 * t] = __fmul2_rn(make_float2(u.x, u.y), xx);
+                v[2 * t + 1] = __fmul2_rn(make_float2(u.z, u.w), xx);
+            }
+        };
+        auto fma_tile = [&](const float (&z)[TL], const float2 (&v)[TV / 2]) {
+#pragma unroll
+            for (int jj = 0; jj < TL; ++jj) {
+                const float2 zz = make_float2(z[jj], z[jj]);
+#pragma unroll
+                for (int kk = 0; kk < TV / 2; ++kk) y2[jj][kk] = __ffma2_rn(zz, v[kk], y2[jj][kk]);
+            }
+        };
+        // y += window elements q in [qa, qb) owned by this lane's group (q = step*NG + g).
+        // Stage bookkeeping once per 32 elements; all_valid: every element of the
+        // range is a stored entry (slices), so no per-step bounds test is needed.
+        auto accumulate = [&](int qa, int qb, bool all_valid) {
+            int k0 = (qa >> lg_ng) << lg_ng;
+            while (k0 < qb) {
+                const int s = k0 >> 5;
+                need_stage(s);
+                const unsigned char *st = ring + (size_t)((gst + s) & (HY_NB - 1)) * a.stage_bytes;
+                const int kend = min(qb, (s + 1) << 5);
+                if (all_valid) {
+                    float z0[TL], z1[TL];
+                    float2 v0r[TV / 2], v1r[TV / 2];
+                    load_elem(st, k0 + g, z0, v0r);
+                    for (; k0 < kend; k0 += 2 * NG) {
+                        const bool two = k0 + NG < kend;
+                        if (two) load_elem(st, k0 + NG + g, z1, v1r);
+                        fma_tile(z0, v0r);
+                        if (!two) {
+                            k0 += NG;
+                            break;
                         }
-#pragma unroll
-                        for (int t = 0; t < TV / 4; ++t) {
-                            const float4 u = reinterpret_cast<const float4 *>(rb + v0)[t];
-                            v[4 * t] = u.x;
-                            v[4 * t + 1] = u.y;
-                            v[4 * t + 2] = u.z;
-                            v[4 * t + 3] = u.w;
-                        }
-                    } else {
-                        const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
-                        const float *rb = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kb;
-                        const float *rc = reinterpret_cast<const float *>(st + a.offc + (e >> 2) * a.sc) + (e & 3) * a.Kl;
-                        const float sc = x * ra[ka];
-#pragma unroll
-                        for (int t = 0; t < TL / 4; ++t) {
-                            const float4 u = reinterpret_cast<const float4 *>(rb + kb0)[t];
-                            z[4 * t] = u.x * sc;
-                            z[4 * t + 1] = u.y * sc;
-                            z[4 * t + 2] = u.z * sc;
-                            z[4 * t + 3] = u.w * sc;
-                        }
-#pragma unroll
-                        for (int t = 0; t < TV / 4; ++t) {
-                            const float4 u = reinterpret_cast<const float4 *>(rc + v0)[t];
-                            v[4 * t] = u.x;
-                            v[4 * t + 1] = u.y;
-                            v[4 * t + 2] = u.z;
-                            v[4 * t + 3] = u.w;
+                        if (k0 + 2 * NG < kend) load_elem(st, k0 + 2 * NG + g, z0, v0r);
+                        fma_tile(z1, v1r);
+                    }
+                } else {
+                    for (; k0 < kend; k0 += NG) {
+                        const int q = k0 + g;
+                        if (q >= qa && q < qb) {
+                            float z[TL];
+                            float2 v[TV / 2];
+                            load_elem(st, q, z, v);
+                            fma_tile(z, v);
                         }
                     }
-#pragma unroll
-                    for (int jj = 0; jj < TL; ++jj)
-#pragma unroll
-                        for (int kk = 0; kk < TV; ++kk) y[jj][kk] = fmaf(z[jj], v[kk], y[jj][kk]);
                 }
+                k0 = kend > k0 ? kend : k0;
+                k0 = ((k0 + NG - 1) >> lg_ng) << lg_ng;
             }
         };
 
         if (it < a.nitem_long) {
-            // ---------------- long rows: groups split a row's nonzeros
-            if (p0 == ts) {
+            // ---------------- long rows: groups split a row's nonzeros; a row that
+            // runs into the next item of the same range carries its partial y over
+            if (p0 == ts && !carry) {
                 j = a.item_aux[it];
                 zero_y();
             }
+            carry = false;
             int64_t pos = p0;
             while (pos < p1) {
                 const int64_t rs = a.lrp[j], re = a.lrp[j + 1];
                 const int64_t a1 = min(re, p1);
                 if (a1 <= pos) break;  // descriptors always advance; never spin on bad input
-                accumulate((int)(pos - p0), (int)(a1 - p0));
+                accumulate((int)(pos - p0), (int)(a1 - p0), false);
                 const bool row_end = (a1 == re);
-                if (row_end || a1 == te) {
+                const bool item_end = (a1 == te);
+                if (!row_end && item_end && it + 1 < r1) {
+                    carry = true;  // same row continues in the next item of this range
+                } else if (row_end || item_end) {
                     __syncwarp();
                     for (int o = lpn; o < 32; o <<= 1) {
 #pragma unroll
                         for (int jj = 0; jj < TL; ++jj)
 #pragma unroll
-                            for (int kk = 0; kk < TV; ++kk)
-                                y[jj][kk] += __shfl_xor_sync(0xffffffffu, y[jj][kk], o);
+                            for (int kk = 0; kk < TV / 2; ++kk) {
+                                y2[jj][kk].x += __shfl_xor_sync(0xffffffffu, y2[jj][kk].x, o);
+                                y2[jj][kk].y += __shfl_xor_sync(0xffffffffu, y2[jj][kk].y, o);
+                            }
                     }
                     const int32_t r = a.lrow[j];
-                    const bool full = (rs >= ts) && (re <= te);
-                    const int slot = (j == a.item_aux[it]) ? 0 : 1;
-                    if (g == 0) store_tile(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (it * 2 + slot) * a.Pm);
+                    const bool full = (rs >= lbeg) && (re <= lend);
+                    const int slot = (j == lfirst) ? 0 : 1;
+                    if (g == 0) store_tile(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (rg * 2 + slot) * a.Pm);
                     zero_y();
                     if (row_end) ++j;
                 }
@@ -339,7 +388,7 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
                 const int64_t se = a.sbase[j + 1];
                 const int64_t a1 = min(se, p1);
                 if (a1 <= pos) break;
-                accumulate((int)(pos - p0), (int)(a1 - p0));
+                accumulate((int)(pos - p0), (int)(a1 - p0), true);
                 if (a1 == se) {
                     __syncwarp();
                     const int32_t r = a.srow[j * NG + g];
@@ -366,26 +415,29 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
     }
 }
 
-// A and Y rows of the long rows cut by task boundaries: sum of the pieces in task order.
-__global__ void __launch_bounds__(256) k_span_fix(const int32_t *span, const int32_t *lrow, const int32_t *row_id,
-                                                  const int32_t *item_aux, const float *apart, const float *ypart,
-                                                  int Kn, int Pm, float *A, float *Y) {
+// Y rows of the long rows cut by warp-range boundaries.  Piece of range t0
+// (slot s0) and pieces of ranges t0+1..t1 (slot 0) are summed: warp w adds the
+// pieces t0+1+w, t0+1+w+8, ... in order, then the 8 warp sums and the first
+// piece are added in a fixed order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_span_fix(const int32_t *span, const int32_t *lrow, const int32_t *item_aux,
+                                                  int64_t ipw, const float *ypart, int Pm, float *Y) {
+    extern __shared__ __align__(16) float part[];  // [8][Pm]
     const int b = blockIdx.x;
     const int32_t jl = span[3 * b], t0 = span[3 * b + 1], t1 = span[3 * b + 2];
-    const int s0 = (item_aux[t0] == jl) ? 0 : 1;
+    const int s0 = (item_aux[(int64_t)t0 * ipw] == jl) ? 0 : 1;
     const int32_t r = lrow[jl];
-    if (A)
-        for (int kn = threadIdx.x; kn < Kn; kn += blockDim.x) {
-            double s = apart[((int64_t)t0 * 2 + s0) * Kn + kn];
-            for (int t = t0 + 1; t <= t1; ++t) s += apart[((int64_t)t * 2) * Kn + kn];
-            A[(int64_t)row_id[r] * Kn + kn] = (float)s;
-        }
-    if (Y)
-        for (int e = threadIdx.x; e < Pm; e += blockDim.x) {
-            double s = ypart[((int64_t)t0 * 2 + s0) * Pm + e];
-            for (int t = t0 + 1; t <= t1; ++t) s += ypart[((int64_t)t * 2) * Pm + e];
-            Y[(int64_t)r * Pm + e] = (float)s;
-        }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int e = lane; e < Pm; e += 32) {
+        float s = 0.f;
+        for (int t = t0 + 1 + w; t <= t1; t += 8) s += ypart[((int64_t)t * 2) * Pm + e];
+        part[w * Pm + e] = s;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < Pm; e += blockDim.x) {
+        double s = ypart[((int64_t)t0 * 2 + s0) * Pm + e];
+        for (int q = 0; q < 8; ++q) s += part[q * Pm + e];
+        Y[(int64_t)r * Pm + e] = (float)s;
+    }
 }
 
 // A(row_id[r], :) = G_(n) y_r for every stored row (the TTMcTC output, Eq.
@@ -483,15 +535,24 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
             }
             __syncthreads();
             if (active) {
-                for (int rr = 0; rr < nr; ++rr) {
-                    const float4 u4 = *reinterpret_cast<const float4 *>(Us + rr * Knp + 4 * kq);
-                    const float4 y4 = __ldg(reinterpret_cast<const float4 *>(Y + (rb + rr) * Pm) + eq);
-                    const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
-                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
+                // 8 rows at a time: their loads are all in flight before the FMAs
+                for (int rr0 = 0; rr0 < nr; rr0 += 8) {
+                    float4 yb[8];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
+                    for (int u = 0; u < 8; ++u)
+                        yb[u] = rr0 + u < nr ? __ldg(reinterpret_cast<const float4 *>(Y + (rb + rr0 + u) * Pm) + eq)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(uv[i], yv[k], acc[i][k]);
+                    for (int u = 0; u < 8; ++u) {
+                        if (rr0 + u >= nr) break;
+                        const float4 u4 = *reinterpret_cast<const float4 *>(Us + (rr0 + u) * Knp + 4 * kq);
+                        const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
+                        const float yv[4] = {yb[u].x, yb[u].y, yb[u].z, yb[u].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(uv[i], yv[k], acc[i][k]);
+                    }
                 }
             }
         }
@@ -551,11 +612,7 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
     if (p.TL == TLV && p.TV == TVV) {                                                                       \
         auto kern = k_hyb<NM1, TLV, TVV>;                                                           \
         HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));     \
-        int per_sm = 0;                                                                                     \
-        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, HY_WARPS * 32, L.smem));      \
-        per_sm = std::max(1, std::min(per_sm, 4));                                                          \
-        const int grid = (int)std::max<int64_t>(                                                            \
-            1, std::min<int64_t>((int64_t)c->num_sms * per_sm, ceil_div(std::max<int64_t>(a.nitem, 1), HY_WARPS))); \
+        const int grid = c->num_sms;                                                                        \
         kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(tA, tB, tC, a);                                    \
         c->nlaunch++;                                                                                       \
         HQ_CUDA(cudaGetLastError());                                                                        \
@@ -637,6 +694,8 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.item_aux = M.item_aux;
     a.nitem = M.nitem;
     a.nitem_long = M.nitem_long;
+    a.ipw = M.ipw;
+    a.nrange = M.nrange;
     HybLaunch L = hyb_launch(c, n, p);
     a.bar_off = L.bar_off;
     a.gs_off = L.gs_off;
@@ -656,8 +715,10 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.err = c->dflag + 2;
     HQ_TRY(p.nm1 == 2 ? launch_hyb_nm1<2>(c, n, p, a, L) : launch_hyb_nm1<3>(c, n, p, a, L));
     if (M.nspan > 0) {
-        k_span_fix<<<(unsigned)M.nspan, 256, 0, c->stream>>>(M.span, M.lrow, M.row_id, M.item_aux, nullptr,
-                                                              c->ypart, a.Kn, a.Pm, nullptr, c->Y);
+        const size_t sm = 8 * (size_t)a.Pm * sizeof(float);
+        HQ_CUDA(cudaFuncSetAttribute(k_span_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_span_fix<<<(unsigned)M.nspan, 256, sm, c->stream>>>(M.span, M.lrow, M.item_aux, M.ipw, c->ypart, a.Pm,
+                                                               c->Y);
         c->nlaunch++;
     }
     HQ_CUDA(cudaGetLastError());

@@ -81,8 +81,9 @@ struct ModeStore {
     int64_t nitem = 0, nitem_long = 0;
     int64_t *item_s = nullptr, *item_e = nullptr;  // [nitem] element ranges
     int32_t *item_aux = nullptr;         // long: first long row; slice task: first slice
+    int64_t ipw = 1, nrange = 0;         // warp w processes items [w*ipw, (w+1)*ipw)
     int64_t nspan = 0;
-    int32_t *span = nullptr;             // [3*nspan] (long row j, first task, last task) of rows cut by tasks
+    int32_t *span = nullptr;             // [3*nspan] (long row j, first range, last range) of rows cut by ranges
 };
 
 struct Workspace;  // defined in the pass unit

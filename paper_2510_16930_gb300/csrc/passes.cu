@@ -962,7 +962,8 @@ hoqri_status passes_init(hoqri_ctx *c) {
     HQ_TRY(encode_factor_maps(c));
     // hybrid layout + dense Y for the FP32 modes with a register-tile plan
     int64_t ybytes = 0, ypb = 0;
-    const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 32)));
+    // ~16 work items per resident warp (8 warps per SM) for balance across SMs
+    const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 128)));
     const int64_t T32 = (Tt + 31) & ~(int64_t)31;
     for (int n = 0; n < c->N; ++n) {
         FastTile p;
@@ -972,7 +973,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
         const ModeStore &M = c->ms[n];
         ab = std::max<int64_t>(ab, std::max<int64_t>(M.nitem_long, 1) * 2 * c->K[n] * (int64_t)c->rsize);
         ybytes = std::max<int64_t>(ybytes, M.R * (int64_t)p.Pm * 4);
-        ypb = std::max<int64_t>(ypb, std::max<int64_t>(M.nitem_long, 1) * 2 * (int64_t)p.Pm * 4);
+        ypb = std::max<int64_t>(ypb, std::max<int64_t>(M.nrange, 1) * 2 * (int64_t)p.Pm * 4);
     }
     c->a_part_bytes = ab;
     HQ_TRY(dalloc(c, &c->a_part, c->a_part_bytes));

@@ -99,6 +99,7 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
             W[i * K + i + rem] = s;
         }
     }
+    __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j): one division per pivot
     if (threadIdx.x == 0) broke = 0;
     __syncthreads();
     double dmax = 0.0;
@@ -109,13 +110,16 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
             double d = W[j * K + j];
             for (int i = 0; i < j; ++i) d -= W[i * K + j] * W[i * K + j];
             if (!(d > tiny) || !(dmax > 0.0)) broke = 1;
-            W[j * K + j] = broke ? 1.0 : sqrt(d);
+            const double r = broke ? 1.0 : sqrt(d);
+            W[j * K + j] = r;
+            inv[j] = 1.0 / r;
         }
         __syncthreads();
+        const double ij = inv[j];
         for (int k = j + 1 + threadIdx.x; k < K; k += blockDim.x) {
             double s = W[j * K + k];
             for (int i = 0; i < j; ++i) s -= W[i * K + j] * W[i * K + k];
-            W[j * K + k] = s / W[j * K + j];
+            W[j * K + k] = s * ij;
         }
         __syncthreads();
     }
@@ -126,17 +130,23 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
         }
         return;
     }
-    // Rinv: solve R X = I column by column (upper triangular)
+    // Rinv: solve R X = I column by column (X upper triangular).  R occupies the
+    // upper triangle of W; X(i, col) for i < col goes to the free strictly-lower
+    // entry W(col, i), the diagonal to Xd, so no second K x K array is needed.
+    __shared__ double Xd[HOQRI_MAXK];
     for (int col = threadIdx.x; col < K; col += blockDim.x) {
-        for (int i = K - 1; i >= 0; --i) {
-            if (i > col) {
-                Rinv[i * K + col] = 0.0;
-                continue;
-            }
+        for (int i = col; i >= 0; --i) {
             double s = (i == col) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= col; ++k) s -= W[i * K + k] * Rinv[k * K + col];
-            Rinv[i * K + col] = s / W[i * K + i];
+            for (int k = i + 1; k <= col; ++k) s -= W[i * K + k] * (k == col ? Xd[col] : W[col * K + k]);
+            const double v = s * inv[i];
+            if (i == col) Xd[col] = v;
+            else W[col * K + i] = v;
         }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+        const int i = t / K, col = t - i * K;
+        Rinv[t] = i > col ? 0.0 : (i == col ? Xd[col] : W[col * K + i]);
     }
 }
 
@@ -186,14 +196,14 @@ __global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, i
 }
 
 template <typename T>
-void launch_apply(hoqri_ctx *c, const T *A, int64_t I, int K, const double *Rinv, T *out, int grid) {
-    cudaStream_t st = c->stream;
+void launch_apply(cudaStream_t st, const int32_t *flag, const T *A, int64_t I, int K, const double *Rinv, T *out,
+                  int grid) {
     switch (K) {
-        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
-        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
-        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
-        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, c->dflag); break;
-        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, c->dflag); break;
+        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
+        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
+        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
+        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
+        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag); break;
     }
 }
 
@@ -313,9 +323,11 @@ __global__ void k_gauss(T *out, int64_t n, uint64_t seed, uint32_t stream_id) {
     }
 }
 
-int gram_blocks(int64_t I) {
+// one Gram block per SM at most (the FP64 multiply-adds need every SM; fewer
+// partials keep the Cholesky's reduction short)
+int gram_blocks(int64_t I, int num_sms) {
     int64_t b = ceil_div(I, 256);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(b, MAX_GRAM_BLOCKS));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(b, std::min(num_sms, MAX_GRAM_BLOCKS)));
 }
 
 template <typename T>
@@ -323,7 +335,7 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     const int64_t I = c->dims[n];
     const int K = c->K[n];
     cudaStream_t st = c->stream;
-    const int nb = gram_blocks(I);
+    const int nb = gram_blocks(I, c->num_sms);
     const int64_t rpb = ceil_div(I, nb);
     const int npairs = K * (K + 1) / 2;
     double *Rinv = c->qr_small;
@@ -338,7 +350,7 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
         k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(A, I, K, rpb, c->qr_part, c->dflag);
         k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, Rinv, c->dflag);
         k_householder<T><<<1, HH_TPB, 0, st>>>(A, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
-        launch_apply<T>(c, A, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
+        launch_apply<T>(st, c->dflag, A, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
         c->nlaunch += 4;
     }
     (void)npairs;

@@ -481,24 +481,43 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
             ie.push_back(std::min(t0 + T8, total_long));
             ia.push_back((int32_t)j);
         }
-        for (int64_t jj = 0; jj < nlong; ++jj) {
-            const int64_t a = lrp[jj] / T8, b = (lrp[jj + 1] - 1) / T8;
-            if (a != b) {
-                span.push_back((int32_t)jj);
-                span.push_back((int32_t)a);
-                span.push_back((int32_t)b);
-            }
-        }
     }
     const int64_t nitem_long = (int64_t)is.size();
+    // slice items of about T8 cost units: one per stored element plus P_{-n}/8
+    // per row (the row of Y it writes), so items of many tiny rows stay small
+    int64_t Pm = 1;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) Pm *= c->K[m];
+    const int64_t row_cost = std::max<int64_t>(1, Pm / 8);
     for (int64_t j = 0; j < nslice;) {
-        int64_t k = j;
-        while (k < nslice && sbase[k] - sbase[j] < T8) ++k;
+        int64_t k = j, cost = 0;
+        while (k < nslice && cost < T8) {
+            cost += (sbase[k + 1] - sbase[k]) + (int64_t)SW * row_cost;
+            ++k;
+        }
         is.push_back(sbase[j]);
         ie.push_back(sbase[k]);
         ia.push_back((int32_t)j);
         j = k;
     }
+    // long items: contiguous ranges, one per warp of a fixed grid (8 warps per SM),
+    // so a long row crossing items inside a range carries its partial sum; a long
+    // row crossing a range boundary is completed from per-range pieces.  Slice
+    // items are dealt to the warps in turn.
+    const int64_t W = (int64_t)c->num_sms * 8;
+    const int64_t ipw = std::max<int64_t>(1, (nitem_long + W - 1) / W);
+    const int64_t nrange = std::max<int64_t>(1, (nitem_long + ipw - 1) / ipw);
+    for (int64_t jj = 0; jj < nlong; ++jj) {
+        const int64_t ta = lrp[jj] / T8, tb = (lrp[jj + 1] - 1) / T8;
+        const int64_t ra = ta / ipw, rb = tb / ipw;
+        if (ra != rb) {
+            span.push_back((int32_t)jj);
+            span.push_back((int32_t)ra);
+            span.push_back((int32_t)rb);
+        }
+    }
+    M.ipw = ipw;
+    M.nrange = nrange;
     M.hyb = true;
     M.htotal = total;
     M.nlong = nlong;

@@ -233,3 +233,23 @@ def test_invalid_index_is_rejected():
     with pytest.raises(hoqri.HoqriError) as ei:
         Ctx(dims, idx, np.ones(2), U0, FP64)
     assert ei.value.code == hoqri.HOQRI_ERR_INVALID
+
+
+def test_warp_ranges_with_carry_match_oracle(orc):
+    """1.5M Zipf nonzeros: several work items per warp range, long rows carried across
+    items and completed across ranges; sampled rows of A_n and all of G vs the oracle."""
+    X = inputs.random_sparse((20_000, 10_000, 5_000), 1_500_000, 31, dist="zipf", s=1.1, values="lognormal",
+                             dtype=np.float32, distinct=True)
+    U0 = [u.astype(np.float32) for u in inputs.orthonormal_factors(X.dims, (16, 16, 16), 32)]
+    U0o = [u.astype(np.float64) for u in U0]
+    vo = X.vals.astype(np.float64)
+    with Ctx(X.dims, X.idx, X.vals, U0, FP32) as c:
+        for n in range(3):
+            A = c.ttmctc(n)
+            cnt = np.bincount(X.idx[n], minlength=X.dims[n])
+            heavy = np.argsort(cnt)[-8:]
+            rng = np.random.default_rng(n)
+            rows = np.unique(np.concatenate([heavy, rng.choice(np.flatnonzero(cnt), 24, replace=False)]))
+            ref, G_ref = orc.ttmctc_rows(X.dims, X.idx, vo, U0o, n, rows.astype(np.int32), return_core=True)
+            assert rel(A[rows], ref) <= 1e-5
+        assert rel(c.core(), G_ref) <= 1e-5
