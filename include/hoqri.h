@@ -166,6 +166,44 @@ HOQRI_API hoqri_status hoqri_profile_read(hoqri_ctx *ctx, double *out, int64_t *
 /* Blocks until all work queued on the context's stream has finished. */
 HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
 
+/* Allocation-free orthonormalisation (no counterpart in the paper, which has no
+ * memory-management interface; the arithmetic is the QR step of Alg. 2).
+ *
+ * U_out = Q of the thin QR of A_in with diag(R) > 0, by CholeskyQR2 in FP64,
+ * with no context and no device allocation: no cudaMalloc or cudaFree, no
+ * allocating library call.  It serves callers that cannot allocate device
+ * memory at the point of the call: code running under a fixed device-memory
+ * budget (a server that has partitioned HBM among requests, where an
+ * allocation can fail or evict), or code between the allocation-free
+ * launches of a pre-planned sequence.  hoqri_orthonormalize needs a context,
+ * whose creation allocates, and may allocate a staging buffer per call.
+ *
+ *   prec    HOQRI_FP64 or HOQRI_FP32 (element type of A_in and U_out)
+ *   I, K    A_in is I x K, row-major; 1 <= K <= HOQRI_NOALLOC_MAXK, I >= K
+ *   A_in    device buffer, read only (unless U_out == A_in)
+ *   U_out   device buffer of I x K; equal to A_in (in place) or not
+ *           overlapping it
+ *   stream  cudaStream_t all work is ordered on (NULL: legacy default stream)
+ * Scratch: one file-scope device array of HOQRI_NOALLOC_SCRATCH_BYTES per
+ * device (Gram partials of at most 160 blocks, R^{-1} and two flags).  Every
+ * call sets its two flags to zero itself (cudaMemsetAsync on the stream);
+ * the partials and R^{-1} are fully written before they are read, so nothing
+ * needs to start at zero.  Its address is looked up with cudaGetSymbolAddress
+ * on the first call made on each device (cached afterwards); that first call
+ * must come before any stream capture on the device begins.  Calls whose
+ * work overlaps in time (different streams, or different host threads) share
+ * the one scratch array and race: order them on one stream.
+ * The call waits for the stream to finish, since it reads the breakdown flag.
+ * Errors: HOQRI_ERR_INVALID for a precision other than the two above, K out of
+ * range (the message names the limit), I < K, host or overlapping buffers;
+ * HOQRI_ERR_QR_BREAKDOWN when a Cholesky pivot is not clearly positive (A_in
+ * rank deficient or too ill conditioned; there is no Householder fallback
+ * here, U_out is then unspecified); HOQRI_ERR_CUDA on a CUDA failure. */
+#define HOQRI_NOALLOC_MAXK 32
+#define HOQRI_NOALLOC_SCRATCH_BYTES (160 * 528 * 8 + 32 * 32 * 8 + 256)
+HOQRI_API hoqri_status hoqri_orthonormalize_noalloc(int32_t prec, int64_t I, int32_t K, const void *A_in,
+                                                    void *U_out, void *stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 HOQRI_API const char *hoqri_last_error(void);
 

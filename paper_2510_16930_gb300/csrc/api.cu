@@ -468,6 +468,36 @@ hoqri_status hoqri_orthonormalize(hoqri_ctx *c, int32_t mode, const void *A_in, 
     return HOQRI_OK;
 }
 
+hoqri_status hoqri_orthonormalize_noalloc(int32_t prec, int64_t I, int32_t K, const void *A_in, void *U_out,
+                                          void *stream) {
+    g_last_error.clear();
+    if (prec != HOQRI_FP64 && prec != HOQRI_FP32) {
+        set_error("hoqri_orthonormalize_noalloc: prec must be HOQRI_FP64 or HOQRI_FP32");
+        return HOQRI_ERR_INVALID;
+    }
+    if (K < 1 || K > HOQRI_NOALLOC_MAXK) {
+        set_error("hoqri_orthonormalize_noalloc: K = " + std::to_string(K) + " outside 1.." +
+                  std::to_string(HOQRI_NOALLOC_MAXK) + " (the static scratch holds at most " +
+                  std::to_string(HOQRI_NOALLOC_MAXK) + " columns)");
+        return HOQRI_ERR_INVALID;
+    }
+    if (I < K) {
+        set_error("hoqri_orthonormalize_noalloc: I = " + std::to_string(I) + " < K = " + std::to_string(K));
+        return HOQRI_ERR_INVALID;
+    }
+    if (!is_device_ptr(A_in) || !is_device_ptr(U_out)) {
+        set_error("hoqri_orthonormalize_noalloc: A_in and U_out must be device buffers");
+        return HOQRI_ERR_INVALID;
+    }
+    const uintptr_t bytes = (uintptr_t)I * (uintptr_t)K * (prec == HOQRI_FP64 ? 8u : 4u);
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A_in), u = reinterpret_cast<uintptr_t>(U_out);
+    if (a != u && a < u + bytes && u < a + bytes) {
+        set_error("hoqri_orthonormalize_noalloc: U_out overlaps A_in without being equal to it");
+        return HOQRI_ERR_INVALID;
+    }
+    return orthonormalize_noalloc(prec, I, K, A_in, U_out, static_cast<cudaStream_t>(stream));
+}
+
 hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
     g_last_error.clear();
     HQ_TRY(check_mode(c, 0));

@@ -186,6 +186,9 @@ hoqri_status ttmctc_pass(hoqri_ctx *c, int n, const void *G, void *A_out);
 
 // QR (qr.cu)
 hoqri_status qr_init(hoqri_ctx *c);
+// CholeskyQR2 with scratch in a static device array (no allocation); prec is
+// HOQRI_FP64 or HOQRI_FP32, 1 <= K <= HOQRI_NOALLOC_MAXK, I >= K (checked by the caller)
+hoqri_status orthonormalize_noalloc(int prec, int64_t I, int K, const void *A, void *U, cudaStream_t st);
 hoqri_status orthonormalize(hoqri_ctx *c, int n, void *A_inout, void *U_out);
 hoqri_status init_factors_seeded(hoqri_ctx *c);
 

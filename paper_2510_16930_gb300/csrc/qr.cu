@@ -13,6 +13,7 @@
 //   flag = 1  -> breakdown seen; the Householder kernel runs and sets flag = 2;
 //   flag = 2  -> U is written; every later kernel of this QR returns at once.
 #include <algorithm>
+#include <mutex>
 
 #include "internal.cuh"
 
@@ -392,6 +393,89 @@ hoqri_status init_factors_seeded(hoqri_ctx *c) {
     }
     HQ_CUDA(cudaGetLastError());
     return HOQRI_OK;
+}
+
+// ---- allocation-free CholeskyQR2 (hoqri_orthonormalize_noalloc): the same
+// Gram / Cholesky / apply kernels, with their scratch in one file-scope device
+// array instead of context buffers.  Layout: Gram partials of up to NA_BLOCKS
+// blocks | R^{-1} | flag[2] (on a 256-byte boundary).
+namespace {
+
+constexpr int NA_BLOCKS = 160;
+constexpr int NA_PAIRS = HOQRI_NOALLOC_MAXK * (HOQRI_NOALLOC_MAXK + 1) / 2;
+constexpr size_t NA_PART_BYTES = (size_t)NA_BLOCKS * NA_PAIRS * sizeof(double);
+constexpr size_t NA_RINV_BYTES = (size_t)HOQRI_NOALLOC_MAXK * HOQRI_NOALLOC_MAXK * sizeof(double);
+static_assert(NA_PART_BYTES + NA_RINV_BYTES + 256 == HOQRI_NOALLOC_SCRATCH_BYTES, "scratch layout");
+static_assert(NA_PART_BYTES % 256 == 0 && NA_RINV_BYTES % 256 == 0, "flag alignment");
+static_assert(HOQRI_NOALLOC_MAXK <= HOQRI_MAXK, "kernels are sized for HOQRI_MAXK columns");
+constexpr int NA_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_na_scratch[HOQRI_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_na_mu;
+unsigned char *g_na_addr[NA_MAX_DEVICES];
+int g_na_sms[NA_MAX_DEVICES];
+
+// address of the scratch on the current device: looked up once per device
+hoqri_status na_scratch(unsigned char **p, int *sms) {
+    int dev = 0;
+    HQ_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NA_MAX_DEVICES) {
+        set_error("hoqri_orthonormalize_noalloc: device ordinal " + std::to_string(dev) + " above the supported " +
+                  std::to_string(NA_MAX_DEVICES - 1));
+        return HOQRI_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_addr[dev]) {
+        void *a = nullptr;
+        HQ_CUDA(cudaGetSymbolAddress(&a, g_na_scratch));
+        int n = 0;
+        HQ_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        g_na_sms[dev] = std::max(n, 1);
+        g_na_addr[dev] = static_cast<unsigned char *>(a);
+    }
+    *p = g_na_addr[dev];
+    *sms = g_na_sms[dev];
+    return HOQRI_OK;
+}
+
+template <typename T>
+hoqri_status orthonormalize_noalloc_t(int64_t I, int K, const T *A, T *U, cudaStream_t st) {
+    unsigned char *base = nullptr;
+    int sms = 1;
+    HQ_TRY(na_scratch(&base, &sms));
+    double *part = reinterpret_cast<double *>(base);
+    double *Rinv = reinterpret_cast<double *>(base + NA_PART_BYTES);
+    int32_t *flag = reinterpret_cast<int32_t *>(base + NA_PART_BYTES + NA_RINV_BYTES);
+    const int nb = std::min(gram_blocks(I, sms), NA_BLOCKS);
+    const int64_t rpb = ceil_div(I, nb);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)sms * 8));
+    HQ_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), st));
+    // pass 0: U = A R1^{-1}; pass 1: U = U R2^{-1} (in place, row by row)
+    for (int pass = 0; pass < 2; ++pass) {
+        const T *src = pass == 0 ? A : U;
+        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, part, flag);
+        k_chol<<<1, 256, 0, st>>>(part, nb, K, Rinv, flag);
+        launch_apply<T>(st, flag, src, I, K, Rinv, U, grid);
+    }
+    HQ_CUDA(cudaGetLastError());
+    int32_t f = 0;
+    HQ_CUDA(cudaMemcpyAsync(&f, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    HQ_CUDA(cudaStreamSynchronize(st));
+    if (f != 0) {
+        set_error("hoqri_orthonormalize_noalloc: Cholesky breakdown (A is rank deficient or too ill conditioned "
+                  "for CholeskyQR2)");
+        return HOQRI_ERR_QR_BREAKDOWN;
+    }
+    return HOQRI_OK;
+}
+
+}  // namespace
+
+hoqri_status orthonormalize_noalloc(int prec, int64_t I, int K, const void *A, void *U, cudaStream_t st) {
+    if (prec == HOQRI_FP64)
+        return orthonormalize_noalloc_t<double>(I, K, static_cast<const double *>(A), static_cast<double *>(U), st);
+    return orthonormalize_noalloc_t<float>(I, K, static_cast<const float *>(A), static_cast<float *>(U), st);
 }
 
 }  // namespace hoqri

@@ -25,7 +25,7 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
            "hoqri_iterate", "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
            "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
-           "hoqri_destroy")
+           "hoqri_destroy", "hoqri_orthonormalize_noalloc")
 
 
 class hoqri_options(C.Structure):
@@ -73,11 +73,12 @@ def load(build_if_missing: bool = True):
     L.hoqri_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
     L.hoqri_synchronize.argtypes = [vp]
     L.hoqri_last_error.restype = C.c_char_p
+    L.hoqri_orthonormalize_noalloc.argtypes = [i32, i64, i32, vp, vp, vp]
     L.hoqri_destroy.argtypes = [vp]
     L.hoqri_destroy.restype = None
     for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate",
                  "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_synchronize",
-                 "hoqri_profile_enable", "hoqri_profile_read"):
+                 "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -138,6 +139,11 @@ def hoqri_ttmctc(ctx, mode, A_out):
 
 def hoqri_orthonormalize(ctx, mode, A_in, U_out):
     _check(load().hoqri_orthonormalize(ctx, int(mode), _addr(A_in), _addr(U_out)))
+
+
+def hoqri_orthonormalize_noalloc(prec, I, K, A_in, U_out, stream=0):
+    """No context and no device allocation; A_in and U_out are device buffers."""
+    _check(load().hoqri_orthonormalize_noalloc(int(prec), int(I), int(K), _addr(A_in), _addr(U_out), int(stream)))
 
 
 def hoqri_iterate(ctx, iters, want_hist=True):

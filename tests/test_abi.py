@@ -52,3 +52,13 @@ def test_create_rejects_bad_arguments_without_gpu_work():
         raise AssertionError("expected HOQRI_ERR_RANK")
     except hoqri.HoqriError as e:
         assert e.code == hoqri.HOQRI_ERR_RANK
+
+
+def test_noalloc_rejects_bad_arguments_before_device_work():
+    """Size and precision checks of hoqri_orthonormalize_noalloc come before any CUDA call."""
+    import pytest
+    for prec, I, K, frag in ((hoqri.HOQRI_BF16X3, 10, 4, "prec"), (hoqri.HOQRI_FP64, 100, 33, "32"),
+                             (hoqri.HOQRI_FP32, 100, 0, "K = 0"), (hoqri.HOQRI_FP64, 5, 8, "I = 5 < K = 8")):
+        with pytest.raises(hoqri.HoqriError) as e:
+            hoqri.hoqri_orthonormalize_noalloc(prec, I, K, 0, 0)
+        assert e.value.code == hoqri.HOQRI_ERR_INVALID and frag in str(e.value)
