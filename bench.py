@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--scale", type=float, default=1.0, help="nnz scale of the workload (1.0 = full size)")
     ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--prec", default=None, choices=["fp64", "fp32", "bf16x3"],
+                    help="arithmetic of the run (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
@@ -250,6 +252,8 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     X, U0, cfg = make_workload(args.config, args.scale, rank)
+    if args.prec:
+        cfg = dict(cfg, prec=args.prec)
     prec = prec_of(cfg)
     npdt = np.float64 if prec == hoqri.HOQRI_FP64 else np.float32
     rsize = 8 if prec == hoqri.HOQRI_FP64 else 4

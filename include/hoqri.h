@@ -153,14 +153,18 @@ HOQRI_API hoqri_status hoqri_fit(hoqri_ctx *ctx, double *resid, double *normX2, 
 HOQRI_API hoqri_status hoqri_info(hoqri_ctx *ctx, int64_t *nnz, int64_t *rows, int64_t *device_bytes);
 
 /* Tracing: enable = 1 clears the totals and starts recording a CUDA event pair
- * around every core pass, TTMcTC pass and QR on the context's stream;
- * enable = 0 stops recording.  Cheap enough to leave on during timing. */
+ * around every core pass, TTMcTC pass, QR and nonzero-stream kernel on the
+ * context's stream; enable = 0 stops recording.  Cheap enough to leave on
+ * during timing. */
 HOQRI_API hoqri_status hoqri_profile_enable(hoqri_ctx *ctx, int32_t enable);
 
 /* Totals since the last hoqri_profile_enable(ctx, 1) (synchronises the stream).
- * out (host, NULL or 6 doubles): core-pass ms, core-pass count, TTMcTC-pass ms,
- * TTMcTC-pass count, QR ms, QR count.  kernel_launches (host, may be NULL): the
- * number of kernels the library has launched since hoqri_create. */
+ * out (host, NULL or 8 doubles): core-pass ms, core-pass count, TTMcTC-pass ms,
+ * TTMcTC-pass count, QR ms, QR count, ms and count of the kernel that streams
+ * the nonzeros of a mode into Y_(n) (one launch inside each core or TTMcTC pass
+ * of a mode stored in the sliced layout; 0 for the other modes).
+ * kernel_launches (host, may be NULL): the number of kernels the library has
+ * launched since hoqri_create. */
 HOQRI_API hoqri_status hoqri_profile_read(hoqri_ctx *ctx, double *out, int64_t *kernel_launches);
 
 /* Blocks until all work queued on the context's stream has finished. */

@@ -114,6 +114,7 @@ static void destroy_impl(hoqri_ctx *c) {
     dfree(c->gnorm_part);
     dfree(c->Y);
     dfree(c->ypart);
+    dfree(c->usplit);
     cudaGetLastError();
     delete c;
 }
@@ -292,10 +293,6 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
         set_error("hoqri_create: unknown precision");
         return HOQRI_ERR_INVALID;
     }
-    if (o.prec == HOQRI_BF16X3) {
-        set_error("hoqri_create: HOQRI_BF16X3 is not available in this build");
-        return HOQRI_ERR_UNSUPPORTED;
-    }
     hoqri_ctx *c = new (std::nothrow) hoqri_ctx();
     if (!c) {
         set_error("hoqri_create: host allocation failed");
@@ -309,7 +306,10 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
         c->P *= ranks[n];
     }
     c->opt = o;
-    c->prec = o.prec;
+    // HOQRI_BF16X3 stores and computes like HOQRI_FP32 except the Kronecker
+    // contraction of long rows, which runs on the tensor cores in split BF16
+    c->prec = o.prec == HOQRI_BF16X3 ? HOQRI_FP32 : o.prec;
+    c->mix = o.prec == HOQRI_BF16X3;
     c->rsize = (o.prec == HOQRI_FP64) ? sizeof(double) : sizeof(float);
     c->stream = (cudaStream_t)stream;
     auto fail = [&](hoqri_status s) {
@@ -601,7 +601,7 @@ hoqri_status hoqri_profile_read(hoqri_ctx *c, double *out, int64_t *kernel_launc
     HQ_TRY(check_mode(c, 0));
     HQ_TRY(prof_collect(c));
     if (out)
-        for (int i = 0; i < 6; ++i) out[i] = c->prof[i];
+        for (int i = 0; i < 8; ++i) out[i] = c->prof[i];
     if (kernel_launches) *kernel_launches = c->nlaunch;
     return HOQRI_OK;
 }

@@ -24,6 +24,7 @@
 // memory by TMA bulk copies completing on an mbarrier, double buffered across
 // the warp's windows; all waits are bounded.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -34,9 +35,9 @@ namespace hoqri {
 namespace {
 
 constexpr int HY_WARPS = 8;
-constexpr int HY_W = 256;           // staged elements per window (multiple of 32)
+constexpr int HY_W = 128;           // staged elements per window (multiple of 32)
 constexpr int HY_WB = HY_W + 8;     // floats per staged array
-constexpr int HY_NB = 4;            // factor-row stages in flight per warp (32 nonzeros each), power of two
+constexpr int HY_NB = 4;            // most factor-row stages in flight per warp (32 nonzeros each)
 constexpr size_t HY_SMEM_CAP = 200 * 1024;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -52,7 +53,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *err) {
     const uint32_t a = smem_addr(bar);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < (1 << 21); ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -67,6 +68,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_
     return false;
 }
 
+// byte offset of staged row e: rows of rb bytes with 16 pad bytes after every
+// 2^gs rows (2^gs rows = 128 bytes, or one row if longer), so any 8 consecutive
+// rows start in 8 distinct 16-byte bank groups: row-wise 16-byte loads and
+// ldmatrix over 8 rows are free of bank conflicts
+__device__ __forceinline__ int soff(int e, int rb, int gs) { return e * rb + ((e >> gs) << 4); }
+
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -77,6 +84,8 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
 
 struct HybArgs {
     int Kn, Pm, Kl, Ka, Kb, Kc, GV, lpn;
+    const float *Ua, *Ub, *Uc;  // gathered factors (other modes in ascending order)
+    int Kr0, Kr1, Kr2;          // their ranks (row lengths, powers of two >= 4)
     const int32_t *ia, *ib, *ic;
     const float *vals;
     const int32_t *row_id;
@@ -91,9 +100,12 @@ struct HybArgs {
     int bar_off, gs_off, w_off, w_stride;  // shared memory layout (bytes)
     int meta_bytes;                        // one staged array of a window (HY_WB floats)
     int ring_off, stage_bytes;             // gathered factor rows: NB stages per warp
-    int stage_tx;                          // bytes the gathers of one stage deliver
-    int sa, sb, sc;                        // bytes per 4-row gather slot of Ua / Ub / Uc
+    int nb, lgnb;                          // factor-row stages per warp (2 or 4) and its log2
+    int rb0, rb1, rb2;                     // bytes per staged row of Ua / Ub / Uc (4K)
+    int gs0, gs1, gs2;                     // 16 pad bytes after every 2^gs rows (see soff)
     int offb, offc;                        // offsets of the Ub / Uc rows inside a stage
+    int abuf_off;                          // per-warp split-BF16 A operand (tensor-core path)
+    const float *Ulsplit;                  // last other factor as BF16 (hi | lo) rows, same bytes per row
     const float *Gn;  // [Kn][Pm]
     float *A;
     float *Y;
@@ -102,20 +114,49 @@ struct HybArgs {
     int32_t *err;
 };
 
-// 4 rows (r0..r3) of a 2-D row-major factor, full width, into shared memory.
-__device__ __forceinline__ void gather4(void *dst, const CUtensorMap *tm, int r0, int r1, int r2, int r3,
-                                        uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_addr(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(0), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(smem_addr(bar))
-        : "memory");
+// 16 bytes global -> shared, cached in L1 (the frequent rows of skewed modes
+// are re-read from L1); completion is tracked by an mbarrier arrive below
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
 }
 
-template <int NM1, int TL, int TV>
-__global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ CUtensorMap tmA,
-                                                       const __grid_constant__ CUtensorMap tmB,
-                                                       const __grid_constant__ CUtensorMap tmC, HybArgs a) {
+// arrive on `bar` once every cp.async this thread issued so far has landed
+// (the barrier's expected count includes these arrivals: .noinc)
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// ---- split-BF16 tensor-core helpers (legacy warp-level mma.sync: the per-row
+// tiles are 16 x 16 or 64 x 8, below the 64-row minimum of tcgen05.mma)
+
+// v = hi + lo with hi = bf16(v) and lo = bf16(v - hi) (v - hi is exact in FP32)
+__device__ __forceinline__ void split2(float2 v, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __float22bfloat162_rn(make_float2(v.x - hf.x, v.y - hf.y));
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(smem_addr(p)));
+}
+
+// d += a (16 x 16, row) * b (16 x 8, col), BF16 in, FP32 accumulate
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// MT x NT tiles of 16 x 8 (MT > 0: the long rows use the split-BF16 tensor-core
+// path; MT == 0: FP32 FMA tiles everywhere)
+template <int NM1, int TL, int TV, int MT, int NT>
+__global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -137,11 +178,13 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
     constexpr int NARR = NM1 + 1;
     unsigned char *wbase = smem_raw + a.w_off + (size_t)w * a.w_stride;
     unsigned char *ring = wbase + a.ring_off;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + a.bar_off) + (size_t)w * (2 + HY_NB);
-    uint64_t *sbar = mbar + 2;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + a.bar_off) + (size_t)w * (3 + HY_NB);
+    uint64_t *sbar = mbar + 3;
 
+    // window barriers: one arrival (lane 0's expect_tx); stage barriers: one
+    // arrival per lane (each lane's cp.async completion)
     if (lane == 0)
-        for (int q = 0; q < 2 + HY_NB; ++q) mbar_init(mbar + q, 1);
+        for (int q = 0; q < 3 + HY_NB; ++q) mbar_init(mbar + q, q < 3 ? 1 : 32);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
 
@@ -179,6 +222,56 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
                 p[k4] = make_float4(y2[j][2 * k4].x, y2[j][2 * k4].y, y2[j][2 * k4 + 1].x, y2[j][2 * k4 + 1].y);
         }
     };
+    constexpr int MZ = 16 * (MT > 0 ? MT : 1);
+    constexpr int ARB = 4 * MZ;                          // abuf row: MZ hi, MZ lo (BF16)
+    constexpr int AGS = ARB >= 128 ? 0 : (ARB == 64 ? 1 : 2);  // pad groups as in soff
+    unsigned char *abuf = wbase + a.abuf_off;
+    // The tensor cores add into their FP32 accumulator without rounding to
+    // nearest, so a long chain of mma into one accumulator drifts (relative bias
+    // growing with the chain).  Each group of mma of two 16-nonzero steps goes to
+    // a fresh accumulator dtmp, which is then added to dacc in FP32 (round to
+    // nearest): the chain per accumulator stays 6 mma long.
+    constexpr int KS_FLUSH = 2;
+    float dacc[MT > 0 ? MT : 1][NT > 0 ? NT : 1][4];
+    float dtmp[MT > 0 ? MT : 1][NT > 0 ? NT : 1][4];
+    int ksteps = 0;  // 16-nonzero steps accumulated in dtmp
+    auto zero_d = [&]() {
+#pragma unroll
+        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+#pragma unroll
+            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    dacc[mt][nt][r] = 0.f;
+                    dtmp[mt][nt][r] = 0.f;
+                }
+        ksteps = 0;
+    };
+    auto flush_d = [&]() {
+#pragma unroll
+        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+#pragma unroll
+            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    dacc[mt][nt][r] += dtmp[mt][nt][r];
+                    dtmp[mt][nt][r] = 0.f;
+                }
+        ksteps = 0;
+    };
+    // lane holds D(mt*16 + gq (+8), nt*8 + 2 tq (+1)), gq = lane / 4, tq = lane % 4
+    auto store_d = [&](float *dst) {
+        flush_d();
+        const int gq = lane >> 2, tq = lane & 3;
+#pragma unroll
+        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+#pragma unroll
+            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
+                float *p = dst + (size_t)(mt * 16 + gq) * a.Kl + nt * 8 + 2 * tq;
+                *reinterpret_cast<float2 *>(p) = make_float2(dacc[mt][nt][0], dacc[mt][nt][1]);
+                *reinterpret_cast<float2 *>(p + 8 * a.Kl) = make_float2(dacc[mt][nt][2], dacc[mt][nt][3]);
+            }
+    };
     bool ok = true;
     int mk = 0;         // meta windows consumed by this warp
     int gst = 0;        // factor-row stages consumed by this warp (wraps harmlessly)
@@ -197,63 +290,114 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
     const int64_t lfirst = (r0 < r1) ? a.item_aux[r0] : -1;
     const int64_t lbeg = (r0 < r1) ? a.item_s[r0] : 0;
     const int64_t lend = (r0 < r1) ? a.item_e[r1 - 1] : 0;
-    int64_t it = (r0 < r1) ? r0 : a.nitem_long + gw;
-    int64_t p0 = it < a.nitem ? a.item_s[it] : 0;
-    if (it < a.nitem) issue_meta(p0, min(p0 + (int64_t)HY_W, a.item_e[it]), 0);
-    int64_t j = 0;
-    bool carry = false;  // a long row continues from the previous item of this range
-    while (it < a.nitem) {
-        const int mbuf = mk & 1;
-        const int64_t ts = a.item_s[it], te = a.item_e[it];
-        const int64_t p1 = min(p0 + (int64_t)HY_W, te);
-        int64_t nit = it, np0 = p0 + HY_W;
-        if (np0 >= te) {
-            nit = next_item(it);
-            np0 = nit < a.nitem ? a.item_s[nit] : 0;
+    // windows of the work list: item, first element, length, item end; the
+    // index/value streams of window k+2 are requested while window k is used
+    struct Win {
+        int64_t it, p0, te;
+        int len;
+        bool first;  // first window of its item
+    };
+    auto item_win = [&](int64_t item) -> Win {
+        Win w{item, 0, 0, 0, true};
+        if (item < a.nitem) {
+            w.p0 = a.item_s[item];
+            w.te = a.item_e[item];
+            w.len = (int)min((int64_t)HY_W, w.te - w.p0);
         }
-        if (nit < a.nitem) issue_meta(np0, min(np0 + (int64_t)HY_W, a.item_e[nit]), mbuf ^ 1);
-        if (!mbar_wait(mbar + mbuf, (uint32_t)((mk >> 1) & 1), a.err)) {
+        return w;
+    };
+    auto next_win = [&](const Win &w) -> Win {
+        if (w.len == 0) return w;
+        const int64_t np0 = w.p0 + HY_W;
+        if (np0 < w.te) return Win{w.it, np0, w.te, (int)min((int64_t)HY_W, w.te - np0), false};
+        return item_win(next_item(w.it));
+    };
+    Win W0 = item_win((r0 < r1) ? r0 : a.nitem_long + gw);
+    Win W1 = next_win(W0);
+    int issued = 0;  // windows whose streams were requested (buffer = window index mod 3)
+    if (W0.len > 0) issue_meta(W0.p0, W0.p0 + W0.len, 0), ++issued;
+    if (W1.len > 0) issue_meta(W1.p0, W1.p0 + W1.len, 1), ++issued;
+    int64_t j = 0;
+    int64_t jc = -1, crs = 0, cre = 0;  // cached bounds (lrp or sbase) of row / slice jc
+    bool carry = false;  // a long row continues from the previous item of this range
+    int pre = 0;         // stages of the current window issued during the previous one
+    int b0 = 0, b1 = 1, b2 = 2;  // meta buffers of windows mk, mk+1, mk+2
+    while (W0.len > 0) {
+        const Win W2 = next_win(W1);
+        if (W2.len > 0) issue_meta(W2.p0, W2.p0 + W2.len, b2), ++issued;
+        if (!mbar_wait(mbar + b0, (uint32_t)((mk / 3) & 1), a.err)) {
             ok = false;
             break;
         }
-        const unsigned char *mb = wbase + (size_t)mbuf * NARR * a.meta_bytes;
-        const int32_t *mia = reinterpret_cast<const int32_t *>(mb);
-        const int32_t *mib = reinterpret_cast<const int32_t *>(mb + a.meta_bytes);
-        const int32_t *mic = reinterpret_cast<const int32_t *>(mb + 2 * a.meta_bytes);
+        const int64_t it = W0.it, nit = W1.it;
+        const int64_t p0 = W0.p0, te = W0.te;
+        const int64_t p1 = p0 + W0.len;
+        const unsigned char *mb = wbase + (size_t)b0 * NARR * a.meta_bytes;
+        const unsigned char *mbn = wbase + (size_t)b1 * NARR * a.meta_bytes;
         const float *mval = reinterpret_cast<const float *>(mb + (NARR - 1) * a.meta_bytes);
-        const int len = (int)(p1 - p0);
+        const int len = W0.len, len_n = W1.len;
         const int nst = (len + 31) >> 5;
+        const int nst_n = (len_n + 31) >> 5;
+        const bool mixw = MT > 0 && it < a.nitem_long;    // window staged for the tensor-core path
+        const bool mixw_n = MT > 0 && nit < a.nitem_long;
+        bool next_meta = false;  // the next window's indices have landed (waited for)
+        int pre_next = 0;
 
-        // gather the factor rows of stage s (elements 32s .. 32s+31 of the window)
-        auto issue_stage = [&](int s) {
-            const int slot = (gst + s) & (HY_NB - 1);
-            unsigned char *st = ring + (size_t)slot * a.stage_bytes;
-            __syncwarp();
-            if (lane == 0) mbar_expect_tx(sbar + slot, (uint32_t)a.stage_tx);
-            __syncwarp();
-            if (lane < 8 * NM1) {
-                const int arr = lane >> 3, gi = lane & 7;
-                const int e0 = 32 * s + 4 * gi;
-                const int32_t *src = arr == 0 ? mia : (arr == 1 ? mib : mic);
-                int r[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) r[q] = (e0 + q < len) ? src[e0 + q] : 0;
-                const CUtensorMap *tm = arr == 0 ? &tmA : (arr == 1 ? &tmB : &tmC);
-                const int sz = arr == 0 ? a.sa : (arr == 1 ? a.sb : a.sc);
-                const int off = arr == 0 ? 0 : (arr == 1 ? a.offb : a.offc);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                gather4(st + off + (size_t)gi * sz, tm, r[0], r[1], r[2], r[3], sbar + slot);
+        // copy the factor rows of elements eb .. eb+31 of a window (meta m, length
+        // ln): a row of K floats is K/4 16-byte chunks; lane takes chunk (lane mod
+        // K/4) of elements lane/(K/4) + t*(128/K), so each row is read by adjacent lanes
+        auto copy_rows = [&](unsigned char *dst, const int32_t *sidx, const float *U, int K, int gsh, int eb, int ln) {
+            const int lg = 31 - __clz(K >> 2);
+            const int qtr = lane & ((K >> 2) - 1);
+            const int e1 = lane >> lg, epl = 32 >> lg;
+            for (int t = 0; t < (K >> 2); ++t) {
+                const int e = e1 + t * epl;
+                if (eb + e < ln) cp_async16(dst + soff(e, 4 * K, gsh) + qtr * 16, U + (size_t)sidx[eb + e] * K + qtr * 4);
             }
         };
-        for (int s = 0; s < nst && s < HY_NB; ++s) issue_stage(s);
+        // stage t of this window; t >= nst: stage t - nst of the next window (the
+        // stream of stages runs on across windows, so no window starts empty)
+        auto issue_stage = [&](int t) {
+            const int slot = (gst + t) & (a.nb - 1);
+            unsigned char *st = ring + (size_t)slot * a.stage_bytes;
+            const unsigned char *m = mb;
+            int ln = len, eb = 32 * t;
+            bool mx = mixw;
+            if (t >= nst) {
+                if (!next_meta) {
+                    if (ok && !mbar_wait(mbar + b1, (uint32_t)(((mk + 1) / 3) & 1), a.err)) ok = false;
+                    next_meta = true;
+                }
+                m = mbn;
+                ln = len_n;
+                eb = 32 * (t - nst);
+                mx = mixw_n;
+                ++pre_next;
+            }
+            const int32_t *sa = reinterpret_cast<const int32_t *>(m);
+            const int32_t *sb = reinterpret_cast<const int32_t *>(m + a.meta_bytes);
+            const int32_t *sc = reinterpret_cast<const int32_t *>(m + 2 * a.meta_bytes);
+            __syncwarp();  // every lane is done reading the slot's previous stage
+            if (NM1 == 2) {
+                copy_rows(st, sa, a.Ua, a.Kr0, a.gs0, eb, ln);
+                copy_rows(st + a.offb, sb, mx ? a.Ulsplit : a.Ub, a.Kr1, a.gs1, eb, ln);
+            } else {
+                copy_rows(st, sa, a.Ua, a.Kr0, a.gs0, eb, ln);
+                copy_rows(st + a.offb, sb, a.Ub, a.Kr1, a.gs1, eb, ln);
+                copy_rows(st + a.offc, sc, mx ? a.Ulsplit : a.Uc, a.Kr2, a.gs2, eb, ln);
+            }
+            cp_async_arrive(sbar + slot);
+        };
+        for (int s = pre; s < nst + nst_n && s < a.nb; ++s) issue_stage(s);
         int cur = -1;  // highest stage waited for in this window
         // make stage s readable; release (re-issue) the stages before it
         auto need_stage = [&](int s) {
             while (cur < s) {
-                if (cur >= 0 && cur + HY_NB < nst) issue_stage(cur + HY_NB);
+                if (cur >= 0 && cur + a.nb < nst + nst_n) issue_stage(cur + a.nb);
                 ++cur;
-                const int slot = (gst + cur) & (HY_NB - 1);
-                if (!mbar_wait(sbar + slot, (uint32_t)(((gst + cur) >> 2) & 1), a.err)) ok = false;
+                const int slot = (gst + cur) & (a.nb - 1);
+                // after a timed-out wait the warp stops waiting and leaves at the window end
+                if (ok && !mbar_wait(sbar + slot, (uint32_t)(((gst + cur) >> a.lgnb) & 1), a.err)) ok = false;
             }
         };
         // operands of window element q (its stage has landed): z = x * (Kronecker
@@ -264,15 +408,15 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
             const float *rz;
             const float4 *rv;
             if (NM1 == 2) {
-                rz = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka + l0;
+                rz = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0)) + l0;
                 rv = reinterpret_cast<const float4 *>(
-                    reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kl + v0);
+                    reinterpret_cast<const float *>(st + a.offb + soff(e, a.rb1, a.gs1)) + v0);
             } else {
-                const float *ra = reinterpret_cast<const float *>(st + (e >> 2) * a.sa) + (e & 3) * a.Ka;
+                const float *ra = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0));
                 x *= ra[ka];
-                rz = reinterpret_cast<const float *>(st + a.offb + (e >> 2) * a.sb) + (e & 3) * a.Kb + kb0;
+                rz = reinterpret_cast<const float *>(st + a.offb + soff(e, a.rb1, a.gs1)) + kb0;
                 rv = reinterpret_cast<const float4 *>(
-                    reinterpret_cast<const float *>(st + a.offc + (e >> 2) * a.sc) + (e & 3) * a.Kl + v0);
+                    reinterpret_cast<const float *>(st + a.offc + soff(e, a.rb2, a.gs2)) + v0);
             }
 #pragma unroll
             for (int t = 0; t < TL / 4; ++t) {
@@ -299,57 +443,242 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
             }
         };
         // y += window elements q in [qa, qb) owned by this lane's group (q = step*NG + g).
-        // Stage bookkeeping once per 32 elements; all_valid: every element of the
-        // range is a stored entry (slices), so no per-step bounds test is needed.
+        // Stage bookkeeping once per 32 elements.  Steps whose NG elements all lie
+        // in [qa, qb) run software-pipelined without tests; only a step cut by qa
+        // or by the end of the range tests its element.  all_valid: every element
+        // of the range is a stored entry (slices; their rows are NG-aligned).
+        auto one_step = [&](const unsigned char *st, int q, int lo, int hi) {
+            if (q >= lo && q < hi) {
+                float z[TL];
+                float2 v[TV / 2];
+                load_elem(st, q, z, v);
+                fma_tile(z, v);
+            }
+        };
         auto accumulate = [&](int qa, int qb, bool all_valid) {
             int k0 = (qa >> lg_ng) << lg_ng;
             while (k0 < qb) {
                 const int s = k0 >> 5;
                 need_stage(s);
-                const unsigned char *st = ring + (size_t)((gst + s) & (HY_NB - 1)) * a.stage_bytes;
+                const unsigned char *st = ring + (size_t)((gst + s) & (a.nb - 1)) * a.stage_bytes;
                 const int kend = min(qb, (s + 1) << 5);
-                if (all_valid) {
+                if (!all_valid && k0 < qa) {
+                    one_step(st, k0 + g, qa, kend);
+                    k0 += NG;
+                }
+                const int kfull = all_valid ? kend : k0 + ((max(kend - k0, 0) >> lg_ng) << lg_ng);
+                if (k0 < kfull) {
                     float z0[TL], z1[TL];
                     float2 v0r[TV / 2], v1r[TV / 2];
                     load_elem(st, k0 + g, z0, v0r);
-                    for (; k0 < kend; k0 += 2 * NG) {
-                        const bool two = k0 + NG < kend;
+                    for (; k0 < kfull; k0 += 2 * NG) {
+                        const bool two = k0 + NG < kfull;
                         if (two) load_elem(st, k0 + NG + g, z1, v1r);
                         fma_tile(z0, v0r);
                         if (!two) {
                             k0 += NG;
                             break;
                         }
-                        if (k0 + 2 * NG < kend) load_elem(st, k0 + 2 * NG + g, z0, v0r);
+                        if (k0 + 2 * NG < kfull) load_elem(st, k0 + 2 * NG + g, z0, v0r);
                         fma_tile(z1, v1r);
                     }
-                } else {
-                    for (; k0 < kend; k0 += NG) {
-                        const int q = k0 + g;
-                        if (q >= qa && q < qb) {
-                            float z[TL];
-                            float2 v[TV / 2];
-                            load_elem(st, q, z, v);
-                            fma_tile(z, v);
-                        }
-                    }
+                }
+                if (!all_valid && k0 < kend) {
+                    one_step(st, k0 + g, qa, kend);
+                    k0 += NG;
                 }
                 k0 = kend > k0 ? kend : k0;
                 k0 = ((k0 + NG - 1) >> lg_ng) << lg_ng;
             }
         };
 
-        if (it < a.nitem_long) {
+        // ---- split-BF16 tensor-core accumulation (long rows, MT > 0).  The row's
+        // tile D (Mz x Kl, Mz = P_{-n}/Kl) accumulates over the row's nonzeros k:
+        //   D += A B,  A(m, k) = x_k * (Kronecker prefix rows of k)(m),  B(k, :) = U_l row of k
+        // with A = Ah + Al and B = Bh + Bl split into BF16 and D += Ah Bh + Ah Bl + Al Bh
+        // in FP32 (the Al Bl term is below FP32 rounding of the sum).  B comes
+        // pre-split from Ulsplit; A is formed and split per 16 nonzeros into abuf.
+        // A rows of the 16 nonzeros k0 .. k0+15 into abuf: lane takes nonzero
+        // lane % 16 and half lane / 16 of its MZ entries
+        auto prep_a = [&](const unsigned char *st, int k0) {
+            const int el = lane & 15, h = lane >> 4;
+            const int q = k0 + el;
+            const int e = q & 31;
+            const float x = mval[q];
+            constexpr int HV = MZ / 2;
+            uint32_t hi[HV / 2], lo[HV / 2];
+            if (NM1 == 2) {
+                const float4 *src = reinterpret_cast<const float4 *>(st + soff(e, a.rb0, a.gs0)) + h * (HV / 4);
+#pragma unroll
+                for (int t = 0; t < HV / 4; ++t) {
+                    const float4 u = src[t];
+                    split2(__fmul2_rn(make_float2(u.x, u.y), make_float2(x, x)), hi[2 * t], lo[2 * t]);
+                    split2(__fmul2_rn(make_float2(u.z, u.w), make_float2(x, x)), hi[2 * t + 1], lo[2 * t + 1]);
+                }
+            } else {
+                // MZ = Ka * Kb with Kb = TL = 8: half h covers prefix index p in [h Ka/2, (h+1) Ka/2)
+                const float *ra = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0));
+                const float4 *rb = reinterpret_cast<const float4 *>(st + a.offb + soff(e, a.rb1, a.gs1));
+                const float4 b0 = rb[0], b1 = rb[1];
+#pragma unroll
+                for (int pp = 0; pp < HV / 8; ++pp) {
+                    const float xa = x * ra[h * (HV / 8) + pp];
+                    const float2 xx = make_float2(xa, xa);
+                    split2(__fmul2_rn(make_float2(b0.x, b0.y), xx), hi[4 * pp], lo[4 * pp]);
+                    split2(__fmul2_rn(make_float2(b0.z, b0.w), xx), hi[4 * pp + 1], lo[4 * pp + 1]);
+                    split2(__fmul2_rn(make_float2(b1.x, b1.y), xx), hi[4 * pp + 2], lo[4 * pp + 2]);
+                    split2(__fmul2_rn(make_float2(b1.z, b1.w), xx), hi[4 * pp + 3], lo[4 * pp + 3]);
+                }
+            }
+            uint4 *dh = reinterpret_cast<uint4 *>(abuf + soff(el, ARB, AGS) + h * HV * 2);
+            uint4 *dl = reinterpret_cast<uint4 *>(abuf + soff(el, ARB, AGS) + MZ * 2 + h * HV * 2);
+#pragma unroll
+            for (int t = 0; t < HV / 8; ++t) {
+                dh[t] = make_uint4(hi[4 * t], hi[4 * t + 1], hi[4 * t + 2], hi[4 * t + 3]);
+                dl[t] = make_uint4(lo[4 * t], lo[4 * t + 1], lo[4 * t + 2], lo[4 * t + 3]);
+            }
+        };
+        // D += contributions of window nonzeros [qa, qb) (one row); k-steps of 16
+        auto mma_accumulate = [&](int qa, int qb) {
+            if constexpr (MT > 0) {
+                const int lm = lane >> 3, lr = lane & 7;  // ldmatrix: matrix lm, row lr
+                const int tq = lane & 3;
+                int k0 = qa & ~15;
+                while (k0 < qb) {
+                    const int s = k0 >> 5;
+                    need_stage(s);
+                    const unsigned char *st = ring + (size_t)((gst + s) & (a.nb - 1)) * a.stage_bytes;
+                    const unsigned char *stl = st + (NM1 == 2 ? a.offb : a.offc);
+                    const int rbl = NM1 == 2 ? a.rb1 : a.rb2, gsl = NM1 == 2 ? a.gs1 : a.gs2;
+                    const int kend = min(qb, (s + 1) << 5);
+                    for (; k0 < kend; k0 += 16) {
+                        prep_a(st, k0);
+                        __syncwarp();
+                        // A fragments: matrices (k 0-7 | 8-15) x (m 0-7 | 8-15) of m-tile mt
+                        uint32_t ah[MT][4], al[MT][4];
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt) {
+                            const unsigned char *pa =
+                                abuf + soff(lr + 8 * (lm >> 1), ARB, AGS) + (mt * 16 + 8 * (lm & 1)) * 2;
+                            ldsm_x4_t(ah[mt], pa);
+                            ldsm_x4_t(al[mt], pa + MZ * 2);
+                        }
+                        // B fragments from the staged split rows (row = nonzero k, n contiguous)
+                        const unsigned char *rowk = stl + soff((k0 & 31) + lr + 8 * (lm & 1), rbl, gsl);
+                        uint32_t bh[NT][2], bl[NT][2];
+                        if (NT == 1) {
+                            uint32_t r4[4];
+                            ldsm_x4_t(r4, rowk + (lm >> 1) * 8 * 2);  // matrices 2, 3: lo half of the row
+                            bh[0][0] = r4[0];
+                            bh[0][1] = r4[1];
+                            bl[0][0] = r4[2];
+                            bl[0][1] = r4[3];
+                        } else {
+#pragma unroll
+                            for (int np = 0; np < NT / 2; ++np) {
+                                uint32_t r4[4];
+                                ldsm_x4_t(r4, rowk + (np * 16 + 8 * (lm >> 1)) * 2);
+                                bh[2 * np][0] = r4[0];
+                                bh[2 * np][1] = r4[1];
+                                bh[2 * np + 1][0] = r4[2];
+                                bh[2 * np + 1][1] = r4[3];
+                                ldsm_x4_t(r4, rowk + (a.Kl + np * 16 + 8 * (lm >> 1)) * 2);
+                                bl[2 * np][0] = r4[0];
+                                bl[2 * np][1] = r4[1];
+                                bl[2 * np + 1][0] = r4[2];
+                                bl[2 * np + 1][1] = r4[3];
+                            }
+                        }
+                        if (k0 < qa || k0 + 16 > kend) {
+                            // nonzeros outside [qa, kend): zero their A and B entries (stale
+                            // staging may hold any bit pattern)
+                            auto ok_k = [&](int k) { return k0 + k >= qa && k0 + k < kend; };
+                            const uint32_t m01 = (ok_k(2 * tq) ? 0xFFFFu : 0u) | (ok_k(2 * tq + 1) ? 0xFFFF0000u : 0u);
+                            const uint32_t m89 =
+                                (ok_k(2 * tq + 8) ? 0xFFFFu : 0u) | (ok_k(2 * tq + 9) ? 0xFFFF0000u : 0u);
+#pragma unroll
+                            for (int mt = 0; mt < MT; ++mt) {
+                                ah[mt][0] &= m01;
+                                ah[mt][1] &= m01;
+                                ah[mt][2] &= m89;
+                                ah[mt][3] &= m89;
+                                al[mt][0] &= m01;
+                                al[mt][1] &= m01;
+                                al[mt][2] &= m89;
+                                al[mt][3] &= m89;
+                            }
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) {
+                                bh[nt][0] &= m01;
+                                bh[nt][1] &= m89;
+                                bl[nt][0] &= m01;
+                                bl[nt][1] &= m89;
+                            }
+                        }
+#pragma unroll
+                        for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+                            for (int nt = 0; nt < NT; ++nt) {
+                                mma_bf16(dtmp[mt][nt], al[mt], bh[nt][0], bh[nt][1]);
+                                mma_bf16(dtmp[mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
+                                mma_bf16(dtmp[mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
+                            }
+                        if (++ksteps == KS_FLUSH) flush_d();
+                        __syncwarp();  // abuf is rewritten by the next k-step
+                    }
+                }
+            }
+        };
+
+        if (MT > 0 && it < a.nitem_long) {
+            // ---------------- long rows on the tensor cores: the whole warp owns the
+            // row's tile; carries across windows and items as in the FMA path below
+            if (W0.first && !carry) {
+                j = a.item_aux[it];
+                zero_d();
+            }
+            carry = false;
+            int64_t pos = p0;
+            while (pos < p1) {
+                if (jc != j) {
+                    jc = j;
+                    crs = a.lrp[j];
+                    cre = a.lrp[j + 1];
+                }
+                const int64_t rs = crs, re = cre;
+                const int64_t a1 = min(re, p1);
+                if (a1 <= pos) break;
+                mma_accumulate((int)(pos - p0), (int)(a1 - p0));
+                const bool row_end = (a1 == re);
+                const bool item_end = (a1 == te);
+                if (!row_end && item_end && it + 1 < r1) {
+                    carry = true;
+                } else if (row_end || item_end) {
+                    const int32_t r = a.lrow[j];
+                    const bool full = (rs >= lbeg) && (re <= lend);
+                    const int slot = (j == lfirst) ? 0 : 1;
+                    store_d(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (rg * 2 + slot) * a.Pm);
+                    zero_d();
+                    if (row_end) ++j;
+                }
+                pos = a1;
+            }
+        } else if (it < a.nitem_long) {
             // ---------------- long rows: groups split a row's nonzeros; a row that
             // runs into the next item of the same range carries its partial y over
-            if (p0 == ts && !carry) {
+            if (W0.first && !carry) {
                 j = a.item_aux[it];
                 zero_y();
             }
             carry = false;
             int64_t pos = p0;
             while (pos < p1) {
-                const int64_t rs = a.lrp[j], re = a.lrp[j + 1];
+                if (jc != j) {
+                    jc = j;
+                    crs = a.lrp[j];
+                    cre = a.lrp[j + 1];
+                }
+                const int64_t rs = crs, re = cre;
                 const int64_t a1 = min(re, p1);
                 if (a1 <= pos) break;  // descriptors always advance; never spin on bad input
                 accumulate((int)(pos - p0), (int)(a1 - p0), false);
@@ -379,13 +708,18 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
             }
         } else {
             // ---------------- slices: lane group g owns row g of the slice
-            if (p0 == ts) {
+            if (W0.first) {
                 j = a.item_aux[it];
                 zero_y();
+                jc = -1;
             }
             int64_t pos = p0;
             while (pos < p1) {
-                const int64_t se = a.sbase[j + 1];
+                if (jc != j) {
+                    jc = j;
+                    cre = a.sbase[j + 1];
+                }
+                const int64_t se = cre;
                 const int64_t a1 = min(se, p1);
                 if (a1 <= pos) break;
                 accumulate((int)(pos - p0), (int)(a1 - p0), true);
@@ -403,16 +737,22 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(const __grid_constant__ C
         need_stage(nst - 1);
         __syncwarp();
         gst += nst;
-        it = nit;
-        p0 = np0;
+        pre = pre_next;
+        W0 = W1;
+        W1 = W2;
+        const int bt = b0;
+        b0 = b1;
+        b1 = b2;
+        b2 = bt;
         ++mk;
         if (!ok) break;
     }
     if (!ok) {
-        // a staged copy never completed: bounded waits for this warp's other copies, then leave
-        mbar_wait(mbar + ((mk + 1) & 1), (uint32_t)(((mk + 1) >> 1) & 1), nullptr);
-        for (int q = 0; q < HY_NB; ++q) mbar_wait(sbar + q, (uint32_t)(((gst + q) >> 2) & 1), nullptr);
+        // a staged copy never completed: bounded waits for this warp's requested
+        // windows that were not consumed, then leave
+        for (int wq = mk; wq < issued; ++wq) mbar_wait(mbar + wq % 3, (uint32_t)((wq / 3) & 1), nullptr);
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Y rows of the long rows cut by warp-range boundaries.  Piece of range t0
@@ -571,10 +911,33 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
 struct HybLaunch {
     size_t smem = 0;
     int bar_off = 0, gs_off = 0, w_off = 0, w_stride = 0, meta_bytes = 0, ring_off = 0, stage_bytes = 0;
-    int stage_tx = 0, sa = 0, sb = 0, sc = 0, offb = 0, offc = 0;
+    int nb = HY_NB, rb0 = 0, rb1 = 0, rb2 = 0, gs0 = 0, gs1 = 0, gs2 = 0, offb = 0, offc = 0, abuf_off = 0;
+    int MT = 0, NT = 0;  // tensor-core tiles of the long rows (0: FP32 FMA tiles)
 };
 
 inline int al128(int x) { return (x + 127) & ~127; }
+
+// Split-BF16 tensor-core tiles for mode n's long rows, if the context computes
+// in HOQRI_BF16X3 and the shape has a kernel: N = 3 with K_a in {16, 32} rows of
+// the tile and K_l in {8, 16, 32} columns; N = 4 with K_a = K_b = 8 (64 rows)
+// and K_l in {8, 16, 32}.  Other shapes keep the FP32 FMA tiles.
+void mix_shape(const hoqri_ctx *c, int n, const FastTile &p, int *MT, int *NT) {
+    *MT = 0;
+    *NT = 0;
+    if (!c->mix || p.TL != 8 || p.TV != 8) return;
+    int K3[3] = {0, 0, 0}, j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) K3[j++] = c->K[m];
+    const int Kl = K3[p.nm1 - 1];
+    if (Kl != 8 && Kl != 16 && Kl != 32) return;
+    if (p.nm1 == 2 && (K3[0] == 16 || K3[0] == 32)) {
+        *MT = K3[0] / 16;
+        *NT = Kl / 8;
+    } else if (p.nm1 == 3 && K3[0] == 8 && K3[1] == 8) {
+        *MT = 4;
+        *NT = Kl / 8;
+    }
+}
 
 HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p) {
     HybLaunch L;
@@ -583,45 +946,78 @@ HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p) {
     int K3[3] = {0, 0, 0}, j = 0;
     for (int m = 0; m < c->N; ++m)
         if (m != n) K3[j++] = c->K[m];
-    L.sa = std::max(16 * K3[0], 128);
-    L.sb = std::max(16 * K3[1], 128);
-    L.sc = p.nm1 == 3 ? std::max(16 * K3[2], 128) : 0;
-    L.offb = 8 * L.sa;
-    L.offc = L.offb + 8 * L.sb;
-    L.stage_bytes = al128(8 * (L.sa + L.sb + L.sc));
-    L.stage_tx = 128 * (K3[0] + K3[1] + (p.nm1 == 3 ? K3[2] : 0));
+    mix_shape(c, n, p, &L.MT, &L.NT);
+    // staged rows: 16 pad bytes after each 128 bytes of rows (soff)
+    auto gsh = [](int K) { return K >= 32 ? 0 : (K == 16 ? 1 : (K == 8 ? 2 : 3)); };
+    auto region = [&](int K) { return 32 * 4 * K + (32 >> gsh(K)) * 16; };
+    L.rb0 = 4 * K3[0];
+    L.rb1 = 4 * K3[1];
+    L.rb2 = p.nm1 == 3 ? 4 * K3[2] : 0;
+    L.gs0 = gsh(K3[0]);
+    L.gs1 = gsh(K3[1]);
+    L.gs2 = p.nm1 == 3 ? gsh(K3[2]) : 0;
+    L.offb = region(K3[0]);
+    L.offc = L.offb + region(K3[1]);
+    L.stage_bytes = al128(L.offc + (p.nm1 == 3 ? region(K3[2]) : 0));
     L.meta_bytes = HY_WB * 4;
     L.bar_off = 0;
-    L.gs_off = al128(HY_WARPS * (2 + HY_NB) * 8);
+    L.gs_off = al128(HY_WARPS * (3 + HY_NB) * 8);
     L.w_off = L.gs_off;
-    L.ring_off = al128(2 * narr * L.meta_bytes);
-    L.w_stride = al128(L.ring_off + HY_NB * L.stage_bytes);
-    L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
+    L.ring_off = al128(3 * narr * L.meta_bytes);
+    const int abuf_bytes = L.MT > 0 ? al128(16 * 64 * L.MT + (L.MT == 1 ? 8 : 16) * 16) : 0;
+    // four stages in flight per warp, two when four do not fit (wide rows)
+    for (L.nb = HY_NB; L.nb >= 2; L.nb /= 2) {
+        L.abuf_off = al128(L.ring_off + L.nb * L.stage_bytes);
+        L.w_stride = al128(L.abuf_off + abuf_bytes);
+        L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
+        if (L.smem <= HY_SMEM_CAP) break;
+    }
+    if (L.nb < 2) L.nb = 2;
     return L;
+}
+
+// U_l as BF16 (hi | lo) rows: out row r = K/2 words of hi pairs, K/2 words of lo pairs
+__global__ void k_split_bf16(const float *U, int64_t rows, int K, uint32_t *out) {
+    const int hk = K / 2;
+    const int64_t npair = rows * hk;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < npair; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / hk;
+        const int cpair = (int)(t - r * hk);
+        uint32_t hi, lo;
+        split2(reinterpret_cast<const float2 *>(U)[t], hi, lo);
+        out[r * K + cpair] = hi;
+        out[r * K + hk + cpair] = lo;
+    }
 }
 
 template <int NM1>
 hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, const HybLaunch &L) {
-    int oth[3] = {0, 0, 0}, j = 0;
-    for (int m = 0; m < c->N; ++m)
-        if (m != n) oth[j++] = m;
-    const CUtensorMap &tA = c->tmap[oth[0]];
-    const CUtensorMap &tB = c->tmap[oth[1]];
-    const CUtensorMap &tC = c->tmap[NM1 == 3 ? oth[2] : oth[0]];
-#define HQ_HYB(TLV, TVV)                                                                                    \
-    if (p.TL == TLV && p.TV == TVV) {                                                                       \
-        auto kern = k_hyb<NM1, TLV, TVV>;                                                           \
-        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));     \
-        const int grid = c->num_sms;                                                                        \
-        kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(tA, tB, tC, a);                                    \
-        c->nlaunch++;                                                                                       \
-        HQ_CUDA(cudaGetLastError());                                                                        \
-        return HOQRI_OK;                                                                                    \
+#define HQ_HYB(TLV, TVV, MTV, NTV)                                                                           \
+    if (p.TL == TLV && p.TV == TVV && L.MT == MTV && L.NT == NTV) {                                          \
+        auto kern = k_hyb<NM1, TLV, TVV, MTV, NTV>;                                                          \
+        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));      \
+        const int grid = c->num_sms;                                                                         \
+        kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                                 \
+        c->nlaunch++;                                                                                        \
+        HQ_CUDA(cudaGetLastError());                                                                         \
+        return HOQRI_OK;                                                                                     \
     }
-    HQ_HYB(8, 8)
-    HQ_HYB(8, 4)
-    HQ_HYB(4, 8)
-    HQ_HYB(4, 4)
+    HQ_HYB(8, 8, 0, 0)
+    HQ_HYB(8, 4, 0, 0)
+    HQ_HYB(4, 8, 0, 0)
+    HQ_HYB(4, 4, 0, 0)
+    if constexpr (NM1 == 2) {
+        HQ_HYB(8, 8, 1, 1)
+        HQ_HYB(8, 8, 1, 2)
+        HQ_HYB(8, 8, 1, 4)
+        HQ_HYB(8, 8, 2, 1)
+        HQ_HYB(8, 8, 2, 2)
+        HQ_HYB(8, 8, 2, 4)
+    } else {
+        HQ_HYB(8, 8, 4, 1)
+        HQ_HYB(8, 8, 4, 2)
+        HQ_HYB(8, 8, 4, 4)
+    }
 #undef HQ_HYB
     set_error("hybrid pass: no kernel for this tile");
     return HOQRI_ERR_UNSUPPORTED;
@@ -629,38 +1025,7 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
 
 }  // namespace
 
-bool hyb_mode(const hoqri_ctx *c, int n) { return c->ms[n].hyb && c->Y != nullptr && c->tmap_ok; }
-
-// One 2-D tensor map per factor U_m (I_m x K_m FP32, row-major), box = one full
-// row, for the gather4 loads of the hybrid pass.  The factors keep their device
-// buffers for the life of the context, so the maps are encoded once.
-hoqri_status encode_factor_maps(hoqri_ctx *c) {
-    c->tmap_ok = false;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        return HOQRI_OK;  // no tensor maps: the modes fall back to the two-pass kernels
-    }
-    auto encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    for (int m = 0; m < c->N; ++m) {
-        if (c->prec != HOQRI_FP32 || c->K[m] % 4 != 0) continue;
-        const cuuint64_t gdim[2] = {(cuuint64_t)c->K[m], (cuuint64_t)c->dims[m]};
-        const cuuint64_t gstride[1] = {(cuuint64_t)c->K[m] * sizeof(float)};
-        const cuuint32_t box[2] = {(cuuint32_t)c->K[m], 1};
-        const cuuint32_t estr[2] = {1, 1};
-        CUresult r = encode(&c->tmap[m], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, c->U[m], gdim, gstride, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) {
-            set_error("cuTensorMapEncodeTiled failed for a factor");
-            return HOQRI_ERR_CUDA;
-        }
-    }
-    c->tmap_ok = true;
-    return HOQRI_OK;
-}
+bool hyb_mode(const hoqri_ctx *c, int n) { return c->ms[n].hyb && c->Y != nullptr; }
 
 // The pass over mode n's hybrid stream: writes every row y_r of Y_(n) into the
 // dense R_n x P_{-n} buffer c->Y (rows cut by task boundaries are completed by
@@ -668,8 +1033,8 @@ hoqri_status encode_factor_maps(hoqri_ctx *c) {
 hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     const ModeStore &M = c->ms[n];
     FastTile p;
-    if (!fast_tile(c, n, &p) || !c->tmap_ok) {
-        set_error("hybrid pass: mode has no register-tile plan or tensor maps");
+    if (!fast_tile(c, n, &p)) {
+        set_error("hybrid pass: mode has no register-tile plan");
         return HOQRI_ERR_UNSUPPORTED;
     }
     HybArgs a{};
@@ -704,16 +1069,53 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.meta_bytes = L.meta_bytes;
     a.ring_off = L.ring_off;
     a.stage_bytes = L.stage_bytes;
-    a.stage_tx = L.stage_tx;
-    a.sa = L.sa;
-    a.sb = L.sb;
-    a.sc = L.sc;
+    a.nb = L.nb;
+    a.lgnb = L.nb == 4 ? 2 : 1;
+    a.rb0 = L.rb0;
+    a.rb1 = L.rb1;
+    a.rb2 = L.rb2;
+    a.gs0 = L.gs0;
+    a.gs1 = L.gs1;
+    a.gs2 = L.gs2;
     a.offb = L.offb;
     a.offc = L.offc;
+    a.abuf_off = L.abuf_off;
+    {
+        int j = 0;
+        const float *Uo[3] = {nullptr, nullptr, nullptr};
+        int Ko[3] = {4, 4, 4};
+        for (int m = 0; m < c->N; ++m)
+            if (m != n) {
+                Uo[j] = (const float *)c->U[m];
+                Ko[j++] = c->K[m];
+            }
+        a.Ua = Uo[0];
+        a.Ub = Uo[1];
+        a.Uc = Uo[2];
+        a.Kr0 = Ko[0];
+        a.Kr1 = Ko[1];
+        a.Kr2 = Ko[2];
+        a.Ulsplit = nullptr;
+        if (L.MT > 0) {
+            // the last other factor, split into BF16 hi / lo rows for the B operand
+            const int Kl = Ko[p.nm1 - 1];
+            int ml = -1;
+            for (int m = c->N - 1; m >= 0 && ml < 0; --m)
+                if (m != n) ml = m;
+            const int64_t rows = c->dims[ml];
+            const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * Kl / 2, 256), 8 * (int64_t)c->num_sms));
+            k_split_bf16<<<grid, 256, 0, c->stream>>>((const float *)c->U[ml], rows, Kl, (uint32_t *)c->usplit);
+            c->nlaunch++;
+            a.Ulsplit = (const float *)c->usplit;
+        }
+    }
     a.Y = c->Y;
     a.ypart = c->ypart;
     a.err = c->dflag + 2;
+    cudaEvent_t e0 = nullptr;
+    HQ_TRY(prof_begin(c, 3, &e0));
     HQ_TRY(p.nm1 == 2 ? launch_hyb_nm1<2>(c, n, p, a, L) : launch_hyb_nm1<3>(c, n, p, a, L));
+    HQ_TRY(prof_end(c, 3, e0));
     if (M.nspan > 0) {
         const size_t sm = 8 * (size_t)a.Pm * sizeof(float);
         HQ_CUDA(cudaFuncSetAttribute(k_span_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));

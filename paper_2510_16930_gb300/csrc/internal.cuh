@@ -98,6 +98,8 @@ struct hoqri_ctx {
     hoqri_options opt{};
     int prec = HOQRI_FP32;
     size_t rsize = 4;                   // sizeof(real)
+    bool mix = false;                   // HOQRI_BF16X3: FP32 storage, split-BF16 tensor-core long rows
+    void *usplit = nullptr;             // BF16 (hi | lo) rows of one factor (tensor-core B operand)
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;
@@ -122,8 +124,6 @@ struct hoqri_ctx {
     double *qr_small = nullptr;         // K x K FP64 workspace (Rinv) and norms
     double *qr_work = nullptr;          // Householder fallback workspace (max I*K doubles)
     double *gnorm_part = nullptr;       // block partials of ||G||^2
-    CUtensorMap tmap[HOQRI_MAXN];       // 2-D maps of the factors for TMA gathers
-    bool tmap_ok = false;
     float *Y = nullptr;                 // rows y_i of Y_(n) for the modes using the hybrid kernels
     int64_t Y_bytes = 0;
     float *ypart = nullptr;             // [nitem_long][2][P_{-n}] pieces of rows cut by long tasks
@@ -146,7 +146,7 @@ struct hoqri_ctx {
         cudaEvent_t a, b;
     };
     std::vector<EvRec> ev_recs;
-    double prof[6] = {0, 0, 0, 0, 0, 0};
+    double prof[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // (ms, count) per trace kind 0..3
 };
 
 namespace hoqri {
@@ -174,7 +174,6 @@ hoqri_status unfold_core(hoqri_ctx *c, int n, const void *G, void *Gn);
 
 // one-stream FP32 passes on the hybrid layout (hybrid.cu)
 bool hyb_mode(const hoqri_ctx *c, int n);
-hoqri_status encode_factor_maps(hoqri_ctx *c);
 hoqri_status hyb_pass(hoqri_ctx *c, int n);
 hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out);
 hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk);
@@ -194,7 +193,7 @@ hoqri_status init_factors_seeded(hoqri_ctx *c);
 
 int64_t ceil_div(int64_t a, int64_t b);
 
-// tracing: kinds 0 = core pass, 1 = TTMcTC pass, 2 = QR
+// tracing: kinds 0 = core pass, 1 = TTMcTC pass, 2 = QR, 3 = nonzero-stream kernel (k_hyb)
 hoqri_status prof_begin(hoqri_ctx *c, int kind, cudaEvent_t *a);
 hoqri_status prof_end(hoqri_ctx *c, int kind, cudaEvent_t a);
 

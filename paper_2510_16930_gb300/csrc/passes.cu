@@ -74,7 +74,7 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
 // bounded wait on an mbarrier phase; false (and *err set) if the limit ran out
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_t *err) {
     const uint32_t a = smem_addr(bar);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < (1 << 21); ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -959,7 +959,6 @@ hoqri_status passes_init(hoqri_ctx *c) {
         if ((int64_t)GEN_WARPS * wst * (int64_t)c->rsize > (int64_t)SMEM_CAP)
             ab = std::max(ab, (int64_t)c->core_grid * GEN_WARPS * c->P * (int64_t)c->rsize);
     }
-    HQ_TRY(encode_factor_maps(c));
     // hybrid layout + dense Y for the FP32 modes with a register-tile plan
     int64_t ybytes = 0, ypb = 0;
     // ~16 work items per resident warp (8 warps per SM) for balance across SMs
@@ -985,6 +984,11 @@ hoqri_status passes_init(hoqri_ctx *c) {
         c->ypart_bytes = ypb;
     }
     HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((c->P + 31) / 32 + 1) * sizeof(double)));
+    if (c->mix && c->Y) {
+        int64_t sb = 0;
+        for (int m = 0; m < c->N; ++m) sb = std::max<int64_t>(sb, c->dims[m] * c->K[m] * 4);
+        HQ_TRY(dalloc(c, &c->usplit, sb));
+    }
     return HOQRI_OK;
 }
 

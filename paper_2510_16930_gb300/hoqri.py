@@ -180,10 +180,10 @@ def hoqri_profile_enable(ctx, enable=True):
 
 def hoqri_profile_read(ctx):
     """Returns (dict of per-pass ms/count totals, kernel launches since create)."""
-    out = (C.c_double * 6)()
+    out = (C.c_double * 8)()
     n = C.c_int64()
     _check(load().hoqri_profile_read(ctx, out, C.byref(n)))
-    keys = ("core_ms", "core_n", "ttmctc_ms", "ttmctc_n", "qr_ms", "qr_n")
+    keys = ("core_ms", "core_n", "ttmctc_ms", "ttmctc_n", "qr_ms", "qr_n", "stream_ms", "stream_n")
     return dict(zip(keys, list(out))), n.value
 
 

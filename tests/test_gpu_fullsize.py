@@ -45,3 +45,15 @@ def test_full_c2_fp32_trajectory_tracks_fp64(c2):
     with Ctx(X.dims, X.idx, X.vals, [u.astype(np.float32) for u in U0], hoqri.HOQRI_FP32) as c:
         h32 = c.iterate(iters)
     assert np.max(np.abs(h32 - h64) / h64) <= 1e-6
+
+
+def test_full_c2_mixed_trajectory_tracks_fp64(c2):
+    """The split-BF16 tensor-core path at the full size: final-fit relative error
+    against the FP64 path within 1e-6 (the accuracy target of the mixed form)."""
+    X, U0, cfg = c2
+    iters = 3
+    with Ctx(X.dims, X.idx, X.vals.astype(np.float64), U0, hoqri.HOQRI_FP64) as c:
+        h64 = c.iterate(iters)
+    with Ctx(X.dims, X.idx, X.vals, [u.astype(np.float32) for u in U0], hoqri.HOQRI_BF16X3) as c:
+        hmix = c.iterate(iters)
+    assert np.max(np.abs(hmix - h64) / h64) <= 1e-6
