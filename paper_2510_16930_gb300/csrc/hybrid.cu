@@ -37,7 +37,6 @@ namespace {
 constexpr int HY_WARPS = 8;
 constexpr int HY_W = 128;           // staged elements per window (multiple of 32)
 constexpr int HY_WB = HY_W + 8;     // floats per staged array
-constexpr int HY_NB = 4;            // most factor-row stages in flight per warp (32 nonzeros each)
 constexpr size_t HY_SMEM_CAP = 200 * 1024;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -68,12 +67,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int32_
     return false;
 }
 
-// byte offset of staged row e: rows of rb bytes with 16 pad bytes after every
-// 2^gs rows (2^gs rows = 128 bytes, or one row if longer), so any 8 consecutive
-// rows start in 8 distinct 16-byte bank groups: row-wise 16-byte loads and
-// ldmatrix over 8 rows are free of bank conflicts
-__device__ __forceinline__ int soff(int e, int rb, int gs) { return e * rb + ((e >> gs) << 4); }
-
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -99,12 +92,6 @@ struct HybArgs {
     int64_t ipw, nrange;                   // items per warp range, number of ranges
     int bar_off, gs_off, w_off, w_stride;  // shared memory layout (bytes)
     int meta_bytes;                        // one staged array of a window (HY_WB floats)
-    int ring_off, stage_bytes;             // gathered factor rows: NB stages per warp
-    int nb, lgnb;                          // factor-row stages per warp (2 or 4) and its log2
-    int rb0, rb1, rb2;                     // bytes per staged row of Ua / Ub / Uc (4K)
-    int gs0, gs1, gs2;                     // 16 pad bytes after every 2^gs rows (see soff)
-    int offb, offc;                        // offsets of the Ub / Uc rows inside a stage
-    int abuf_off;                          // per-warp split-BF16 A operand (tensor-core path)
     const float *Ulsplit;                  // last other factor as BF16 (hi | lo) rows, same bytes per row
     const float *Gn;  // [Kn][Pm]
     float *A;
@@ -113,18 +100,6 @@ struct HybArgs {
     float *ypart;  // [nitem_long][2][Pm]
     int32_t *err;
 };
-
-// 16 bytes global -> shared, cached in L1 (the frequent rows of skewed modes
-// are re-read from L1); completion is tracked by an mbarrier arrive below
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
-}
-
-// arrive on `bar` once every cp.async this thread issued so far has landed
-// (the barrier's expected count includes these arrivals: .noinc)
-__device__ __forceinline__ void cp_async_arrive(uint64_t *bar) {
-    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
 
 // ---- split-BF16 tensor-core helpers (legacy warp-level mma.sync: the per-row
 // tiles are 16 x 16 or 64 x 8, below the 64-row minimum of tcgen05.mma)
@@ -138,12 +113,6 @@ __device__ __forceinline__ void split2(float2 v, uint32_t &hi, uint32_t &lo) {
     lo = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-__device__ __forceinline__ void ldsm_x4_t(uint32_t (&r)[4], const void *p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(smem_addr(p)));
-}
-
 // d += a (16 x 16, row) * b (16 x 8, col), BF16 in, FP32 accumulate
 __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
     asm volatile(
@@ -153,10 +122,14 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// MT x NT tiles of 16 x 8 (MT > 0: the long rows use the split-BF16 tensor-core
-// path; MT == 0: FP32 FMA tiles everywhere)
-template <int NM1, int TL, int TV, int MT, int NT>
-__global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
+// One pass over mode n's hybrid stream, part PART: 0 = the long rows (a
+// contiguous range of items per warp), 1 = the slices (every nw-th item).
+// Factor rows are read straight from global memory (L1-cached, read-only path)
+// into registers: at two blocks of 8 warps per SM the loads of one warp overlap
+// the arithmetic of the others.  MT > 0: long rows on the split-BF16 tensor-core
+// path (MT x NT tiles of 16 x 8); MT == 0: FP32 FMA tiles (TL x TV per lane).
+template <int NM1, int TL, int TV, int MT, int NT, int PART>
+__global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
@@ -176,15 +149,12 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         kb0 = l0 - ka * a.Kb;
     }
     constexpr int NARR = NM1 + 1;
+    constexpr bool MMA = MT > 0 && PART == 0;
     unsigned char *wbase = smem_raw + a.w_off + (size_t)w * a.w_stride;
-    unsigned char *ring = wbase + a.ring_off;
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + a.bar_off) + (size_t)w * (3 + HY_NB);
-    uint64_t *sbar = mbar + 3;
-
-    // window barriers: one arrival (lane 0's expect_tx); stage barriers: one
-    // arrival per lane (each lane's cp.async completion)
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + a.bar_off) + (size_t)w * 3;
+    // window barriers: one arrival each (lane 0's expect_tx)
     if (lane == 0)
-        for (int q = 0; q < 3 + HY_NB; ++q) mbar_init(mbar + q, q < 3 ? 1 : 32);
+        for (int q = 0; q < 3; ++q) mbar_init(mbar + q, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     __syncthreads();
 
@@ -205,41 +175,40 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         }
     };
 
-    // y tile as column pairs: y2[j][k] holds columns (2k, 2k+1) of tile row j
-    float2 y2[TL][TV / 2];
+    // ---- FP32 FMA tiles: y tile as column pairs, y2[j][k] = columns (2k, 2k+1) of row j
+    constexpr int TLs = MMA ? 1 : TL, TVs = MMA ? 2 : TV;  // unused by the tensor-core part
+    float2 y2[TLs][TVs / 2];
     auto zero_y = [&]() {
 #pragma unroll
-        for (int j = 0; j < TL; ++j)
+        for (int j = 0; j < TLs; ++j)
 #pragma unroll
-            for (int k = 0; k < TV / 2; ++k) y2[j][k] = make_float2(0.f, 0.f);
+            for (int k = 0; k < TVs / 2; ++k) y2[j][k] = make_float2(0.f, 0.f);
     };
     auto store_tile = [&](float *dst) {
 #pragma unroll
-        for (int j = 0; j < TL; ++j) {
+        for (int j = 0; j < TLs; ++j) {
             float4 *p = reinterpret_cast<float4 *>(dst + (size_t)(l0 + j) * a.Kl + v0);
 #pragma unroll
-            for (int k4 = 0; k4 < TV / 4; ++k4)
+            for (int k4 = 0; k4 < TVs / 4; ++k4)
                 p[k4] = make_float4(y2[j][2 * k4].x, y2[j][2 * k4].y, y2[j][2 * k4 + 1].x, y2[j][2 * k4 + 1].y);
         }
     };
-    constexpr int MZ = 16 * (MT > 0 ? MT : 1);
-    constexpr int ARB = 4 * MZ;                          // abuf row: MZ hi, MZ lo (BF16)
-    constexpr int AGS = ARB >= 128 ? 0 : (ARB == 64 ? 1 : 2);  // pad groups as in soff
-    unsigned char *abuf = wbase + a.abuf_off;
-    // The tensor cores add into their FP32 accumulator without rounding to
-    // nearest, so a long chain of mma into one accumulator drifts (relative bias
-    // growing with the chain).  Each group of mma of two 16-nonzero steps goes to
-    // a fresh accumulator dtmp, which is then added to dacc in FP32 (round to
-    // nearest): the chain per accumulator stays 6 mma long.
+
+    // ---- split-BF16 tensor-core tiles.  The tensor cores add into their FP32
+    // accumulator without rounding to nearest, so a long chain of mma into one
+    // accumulator drifts (a relative bias growing with the chain).  Each group of
+    // mma of two 16-nonzero steps goes to a fresh accumulator dtmp, which is then
+    // added to dacc in FP32 (round to nearest): chains stay 6 mma long.
+    constexpr int MTs = MMA ? MT : 1, NTs = MMA ? NT : 1;
     constexpr int KS_FLUSH = 2;
-    float dacc[MT > 0 ? MT : 1][NT > 0 ? NT : 1][4];
-    float dtmp[MT > 0 ? MT : 1][NT > 0 ? NT : 1][4];
+    float dacc[MTs][NTs][4];
+    float dtmp[MTs][NTs][4];
     int ksteps = 0;  // 16-nonzero steps accumulated in dtmp
     auto zero_d = [&]() {
 #pragma unroll
-        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+        for (int mt = 0; mt < MTs; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt)
+            for (int nt = 0; nt < NTs; ++nt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     dacc[mt][nt][r] = 0.f;
@@ -249,9 +218,9 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
     };
     auto flush_d = [&]() {
 #pragma unroll
-        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+        for (int mt = 0; mt < MTs; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt)
+            for (int nt = 0; nt < NTs; ++nt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     dacc[mt][nt][r] += dtmp[mt][nt][r];
@@ -264,32 +233,28 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         flush_d();
         const int gq = lane >> 2, tq = lane & 3;
 #pragma unroll
-        for (int mt = 0; mt < (MT > 0 ? MT : 1); ++mt)
+        for (int mt = 0; mt < MTs; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < (NT > 0 ? NT : 1); ++nt) {
+            for (int nt = 0; nt < NTs; ++nt) {
                 float *p = dst + (size_t)(mt * 16 + gq) * a.Kl + nt * 8 + 2 * tq;
                 *reinterpret_cast<float2 *>(p) = make_float2(dacc[mt][nt][0], dacc[mt][nt][1]);
                 *reinterpret_cast<float2 *>(p + 8 * a.Kl) = make_float2(dacc[mt][nt][2], dacc[mt][nt][3]);
             }
     };
+    if (MMA) zero_d(); else zero_y();
+
     bool ok = true;
-    int mk = 0;         // meta windows consumed by this warp
-    int gst = 0;        // factor-row stages consumed by this warp (wraps harmlessly)
-    // work of this warp: a contiguous range of long-row items (rows carry across
-    // items inside the range), then every nw-th slice item
+    int mk = 0;  // windows consumed by this warp
+    // work list of this warp: part 0, a contiguous range of long-row items (rows
+    // carry across items inside the range); part 1, every nw-th slice item
     const int64_t rg = gw;
-    const int64_t r0 = rg * a.ipw;
-    const int64_t r1 = rg < a.nrange ? min(r0 + a.ipw, a.nitem_long) : r0;
-    auto next_item = [&](int64_t cur) -> int64_t {
-        if (cur < a.nitem_long) {
-            if (cur + 1 < r1) return cur + 1;
-            return a.nitem_long + gw;
-        }
-        return cur + nw;
-    };
-    const int64_t lfirst = (r0 < r1) ? a.item_aux[r0] : -1;
-    const int64_t lbeg = (r0 < r1) ? a.item_s[r0] : 0;
-    const int64_t lend = (r0 < r1) ? a.item_e[r1 - 1] : 0;
+    const int64_t r0 = PART == 0 ? rg * a.ipw : 0;
+    const int64_t r1 = PART == 0 ? (rg < a.nrange ? min(r0 + a.ipw, a.nitem_long) : r0) : 0;
+    const int64_t iend = PART == 0 ? r1 : a.nitem;
+    auto next_item = [&](int64_t cur) -> int64_t { return PART == 0 ? cur + 1 : cur + nw; };
+    const int64_t lfirst = (PART == 0 && r0 < r1) ? a.item_aux[r0] : -1;
+    const int64_t lbeg = (PART == 0 && r0 < r1) ? a.item_s[r0] : 0;
+    const int64_t lend = (PART == 0 && r0 < r1) ? a.item_e[r1 - 1] : 0;
     // windows of the work list: item, first element, length, item end; the
     // index/value streams of window k+2 are requested while window k is used
     struct Win {
@@ -298,21 +263,21 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         bool first;  // first window of its item
     };
     auto item_win = [&](int64_t item) -> Win {
-        Win w{item, 0, 0, 0, true};
-        if (item < a.nitem) {
-            w.p0 = a.item_s[item];
-            w.te = a.item_e[item];
-            w.len = (int)min((int64_t)HY_W, w.te - w.p0);
+        Win wv{item, 0, 0, 0, true};
+        if (item < iend) {
+            wv.p0 = a.item_s[item];
+            wv.te = a.item_e[item];
+            wv.len = (int)min((int64_t)HY_W, wv.te - wv.p0);
         }
-        return w;
+        return wv;
     };
-    auto next_win = [&](const Win &w) -> Win {
-        if (w.len == 0) return w;
-        const int64_t np0 = w.p0 + HY_W;
-        if (np0 < w.te) return Win{w.it, np0, w.te, (int)min((int64_t)HY_W, w.te - np0), false};
-        return item_win(next_item(w.it));
+    auto next_win = [&](const Win &wv) -> Win {
+        if (wv.len == 0) return wv;
+        const int64_t np0 = wv.p0 + HY_W;
+        if (np0 < wv.te) return Win{wv.it, np0, wv.te, (int)min((int64_t)HY_W, wv.te - np0), false};
+        return item_win(next_item(wv.it));
     };
-    Win W0 = item_win((r0 < r1) ? r0 : a.nitem_long + gw);
+    Win W0 = item_win(PART == 0 ? r0 : a.nitem_long + gw);
     Win W1 = next_win(W0);
     int issued = 0;  // windows whose streams were requested (buffer = window index mod 3)
     if (W0.len > 0) issue_meta(W0.p0, W0.p0 + W0.len, 0), ++issued;
@@ -320,7 +285,6 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
     int64_t j = 0;
     int64_t jc = -1, crs = 0, cre = 0;  // cached bounds (lrp or sbase) of row / slice jc
     bool carry = false;  // a long row continues from the previous item of this range
-    int pre = 0;         // stages of the current window issued during the previous one
     int b0 = 0, b1 = 1, b2 = 2;  // meta buffers of windows mk, mk+1, mk+2
     while (W0.len > 0) {
         const Win W2 = next_win(W1);
@@ -329,98 +293,32 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
             ok = false;
             break;
         }
-        const int64_t it = W0.it, nit = W1.it;
+        const int64_t it = W0.it;
         const int64_t p0 = W0.p0, te = W0.te;
         const int64_t p1 = p0 + W0.len;
         const unsigned char *mb = wbase + (size_t)b0 * NARR * a.meta_bytes;
-        const unsigned char *mbn = wbase + (size_t)b1 * NARR * a.meta_bytes;
+        const int32_t *mia = reinterpret_cast<const int32_t *>(mb);
+        const int32_t *mib = reinterpret_cast<const int32_t *>(mb + a.meta_bytes);
+        const int32_t *mic = reinterpret_cast<const int32_t *>(mb + 2 * a.meta_bytes);
         const float *mval = reinterpret_cast<const float *>(mb + (NARR - 1) * a.meta_bytes);
-        const int len = W0.len, len_n = W1.len;
-        const int nst = (len + 31) >> 5;
-        const int nst_n = (len_n + 31) >> 5;
-        const bool mixw = MT > 0 && it < a.nitem_long;    // window staged for the tensor-core path
-        const bool mixw_n = MT > 0 && nit < a.nitem_long;
-        bool next_meta = false;  // the next window's indices have landed (waited for)
-        int pre_next = 0;
 
-        // copy the factor rows of elements eb .. eb+31 of a window (meta m, length
-        // ln): a row of K floats is K/4 16-byte chunks; lane takes chunk (lane mod
-        // K/4) of elements lane/(K/4) + t*(128/K), so each row is read by adjacent lanes
-        auto copy_rows = [&](unsigned char *dst, const int32_t *sidx, const float *U, int K, int gsh, int eb, int ln) {
-            const int lg = 31 - __clz(K >> 2);
-            const int qtr = lane & ((K >> 2) - 1);
-            const int e1 = lane >> lg, epl = 32 >> lg;
-            for (int t = 0; t < (K >> 2); ++t) {
-                const int e = e1 + t * epl;
-                if (eb + e < ln) cp_async16(dst + soff(e, 4 * K, gsh) + qtr * 16, U + (size_t)sidx[eb + e] * K + qtr * 4);
-            }
-        };
-        // stage t of this window; t >= nst: stage t - nst of the next window (the
-        // stream of stages runs on across windows, so no window starts empty)
-        auto issue_stage = [&](int t) {
-            const int slot = (gst + t) & (a.nb - 1);
-            unsigned char *st = ring + (size_t)slot * a.stage_bytes;
-            const unsigned char *m = mb;
-            int ln = len, eb = 32 * t;
-            bool mx = mixw;
-            if (t >= nst) {
-                if (!next_meta) {
-                    if (ok && !mbar_wait(mbar + b1, (uint32_t)(((mk + 1) / 3) & 1), a.err)) ok = false;
-                    next_meta = true;
-                }
-                m = mbn;
-                ln = len_n;
-                eb = 32 * (t - nst);
-                mx = mixw_n;
-                ++pre_next;
-            }
-            const int32_t *sa = reinterpret_cast<const int32_t *>(m);
-            const int32_t *sb = reinterpret_cast<const int32_t *>(m + a.meta_bytes);
-            const int32_t *sc = reinterpret_cast<const int32_t *>(m + 2 * a.meta_bytes);
-            __syncwarp();  // every lane is done reading the slot's previous stage
-            if (NM1 == 2) {
-                copy_rows(st, sa, a.Ua, a.Kr0, a.gs0, eb, ln);
-                copy_rows(st + a.offb, sb, mx ? a.Ulsplit : a.Ub, a.Kr1, a.gs1, eb, ln);
-            } else {
-                copy_rows(st, sa, a.Ua, a.Kr0, a.gs0, eb, ln);
-                copy_rows(st + a.offb, sb, a.Ub, a.Kr1, a.gs1, eb, ln);
-                copy_rows(st + a.offc, sc, mx ? a.Ulsplit : a.Uc, a.Kr2, a.gs2, eb, ln);
-            }
-            cp_async_arrive(sbar + slot);
-        };
-        for (int s = pre; s < nst + nst_n && s < a.nb; ++s) issue_stage(s);
-        int cur = -1;  // highest stage waited for in this window
-        // make stage s readable; release (re-issue) the stages before it
-        auto need_stage = [&](int s) {
-            while (cur < s) {
-                if (cur >= 0 && cur + a.nb < nst + nst_n) issue_stage(cur + a.nb);
-                ++cur;
-                const int slot = (gst + cur) & (a.nb - 1);
-                // after a timed-out wait the warp stops waiting and leaves at the window end
-                if (ok && !mbar_wait(sbar + slot, (uint32_t)(((gst + cur) >> a.lgnb) & 1), a.err)) ok = false;
-            }
-        };
-        // operands of window element q (its stage has landed): z = x * (Kronecker
-        // prefix rows), v = last other mode's row, both restricted to the lane's tile
-        auto load_elem = [&](const unsigned char *st, int q, float (&z)[TL], float2 (&v)[TV / 2]) {
-            const int e = q & 31;
+        // operands of window element q: z = x * (Kronecker prefix rows), v = the
+        // last other mode's row, both restricted to the lane's tile
+        auto load_elem = [&](int q, float (&z)[TLs], float2 (&v)[TVs / 2]) {
             float x = mval[q];
             const float *rz;
             const float4 *rv;
             if (NM1 == 2) {
-                rz = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0)) + l0;
-                rv = reinterpret_cast<const float4 *>(
-                    reinterpret_cast<const float *>(st + a.offb + soff(e, a.rb1, a.gs1)) + v0);
+                rz = a.Ua + (size_t)mia[q] * a.Kr0 + l0;
+                rv = reinterpret_cast<const float4 *>(a.Ub + (size_t)mib[q] * a.Kr1 + v0);
             } else {
-                const float *ra = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0));
-                x *= ra[ka];
-                rz = reinterpret_cast<const float *>(st + a.offb + soff(e, a.rb1, a.gs1)) + kb0;
-                rv = reinterpret_cast<const float4 *>(
-                    reinterpret_cast<const float *>(st + a.offc + soff(e, a.rb2, a.gs2)) + v0);
+                x *= __ldg(a.Ua + (size_t)mia[q] * a.Kr0 + ka);
+                rz = a.Ub + (size_t)mib[q] * a.Kr1 + kb0;
+                rv = reinterpret_cast<const float4 *>(a.Uc + (size_t)mic[q] * a.Kr2 + v0);
             }
 #pragma unroll
-            for (int t = 0; t < TL / 4; ++t) {
-                const float4 u = reinterpret_cast<const float4 *>(rz)[t];
+            for (int t = 0; t < TLs / 4; ++t) {
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(rz) + t);
                 z[4 * t] = u.x;
                 z[4 * t + 1] = u.y;
                 z[4 * t + 2] = u.z;
@@ -428,247 +326,132 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
             }
             const float2 xx = make_float2(x, x);
 #pragma unroll
-            for (int t = 0; t < TV / 4; ++t) {
-                const float4 u = rv[t];
+            for (int t = 0; t < TVs / 4; ++t) {
+                const float4 u = __ldg(rv + t);
                 v[2 * t] = __fmul2_rn(make_float2(u.x, u.y), xx);
                 v[2 * t + 1] = __fmul2_rn(make_float2(u.z, u.w), xx);
             }
         };
-        auto fma_tile = [&](const float (&z)[TL], const float2 (&v)[TV / 2]) {
+        auto fma_tile = [&](const float (&z)[TLs], const float2 (&v)[TVs / 2]) {
 #pragma unroll
-            for (int jj = 0; jj < TL; ++jj) {
+            for (int jj = 0; jj < TLs; ++jj) {
                 const float2 zz = make_float2(z[jj], z[jj]);
 #pragma unroll
-                for (int kk = 0; kk < TV / 2; ++kk) y2[jj][kk] = __ffma2_rn(zz, v[kk], y2[jj][kk]);
+                for (int kk = 0; kk < TVs / 2; ++kk) y2[jj][kk] = __ffma2_rn(zz, v[kk], y2[jj][kk]);
             }
         };
-        // y += window elements q in [qa, qb) owned by this lane's group (q = step*NG + g).
-        // Stage bookkeeping once per 32 elements.  Steps whose NG elements all lie
-        // in [qa, qb) run software-pipelined without tests; only a step cut by qa
-        // or by the end of the range tests its element.  all_valid: every element
-        // of the range is a stored entry (slices; their rows are NG-aligned).
-        auto one_step = [&](const unsigned char *st, int q, int lo, int hi) {
+        auto one_step = [&](int q, int lo, int hi) {
             if (q >= lo && q < hi) {
-                float z[TL];
-                float2 v[TV / 2];
-                load_elem(st, q, z, v);
+                float z[TLs];
+                float2 v[TVs / 2];
+                load_elem(q, z, v);
                 fma_tile(z, v);
             }
         };
+        // y += window elements q in [qa, qb) owned by this lane's group (q = step*NG + g).
+        // Steps whose NG elements all lie in [qa, qb) run software-pipelined (the
+        // loads of the next step are issued before the multiply-adds of this
+        // one); a step cut by qa or qb tests its element.  all_valid: every
+        // element of the range is a stored entry (slices; their rows are NG-aligned).
         auto accumulate = [&](int qa, int qb, bool all_valid) {
             int k0 = (qa >> lg_ng) << lg_ng;
-            while (k0 < qb) {
-                const int s = k0 >> 5;
-                need_stage(s);
-                const unsigned char *st = ring + (size_t)((gst + s) & (a.nb - 1)) * a.stage_bytes;
-                const int kend = min(qb, (s + 1) << 5);
-                if (!all_valid && k0 < qa) {
-                    one_step(st, k0 + g, qa, kend);
-                    k0 += NG;
-                }
-                const int kfull = all_valid ? kend : k0 + ((max(kend - k0, 0) >> lg_ng) << lg_ng);
-                if (k0 < kfull) {
-                    float z0[TL], z1[TL];
-                    float2 v0r[TV / 2], v1r[TV / 2];
-                    load_elem(st, k0 + g, z0, v0r);
-                    for (; k0 < kfull; k0 += 2 * NG) {
-                        const bool two = k0 + NG < kfull;
-                        if (two) load_elem(st, k0 + NG + g, z1, v1r);
-                        fma_tile(z0, v0r);
-                        if (!two) {
-                            k0 += NG;
-                            break;
-                        }
-                        if (k0 + 2 * NG < kfull) load_elem(st, k0 + 2 * NG + g, z0, v0r);
-                        fma_tile(z1, v1r);
-                    }
-                }
-                if (!all_valid && k0 < kend) {
-                    one_step(st, k0 + g, qa, kend);
-                    k0 += NG;
-                }
-                k0 = kend > k0 ? kend : k0;
-                k0 = ((k0 + NG - 1) >> lg_ng) << lg_ng;
+            if (!all_valid && k0 < qa) {
+                one_step(k0 + g, qa, qb);
+                k0 += NG;
             }
+            const int kfull = all_valid ? qb : k0 + ((max(qb - k0, 0) >> lg_ng) << lg_ng);
+            if (k0 < kfull) {
+                float z0[TLs], z1[TLs];
+                float2 v0r[TVs / 2], v1r[TVs / 2];
+                load_elem(k0 + g, z0, v0r);
+                for (; k0 < kfull; k0 += 2 * NG) {
+                    const bool two = k0 + NG < kfull;
+                    if (two) load_elem(k0 + NG + g, z1, v1r);
+                    fma_tile(z0, v0r);
+                    if (!two) {
+                        k0 += NG;
+                        break;
+                    }
+                    if (k0 + 2 * NG < kfull) load_elem(k0 + 2 * NG + g, z0, v0r);
+                    fma_tile(z1, v1r);
+                }
+            }
+            if (!all_valid && k0 < qb) one_step(k0 + g, qa, qb);
         };
 
-        // ---- split-BF16 tensor-core accumulation (long rows, MT > 0).  The row's
-        // tile D (Mz x Kl, Mz = P_{-n}/Kl) accumulates over the row's nonzeros k:
+        // D += contributions of window nonzeros [qa, qb) of one row on the tensor
+        // cores, 16 nonzeros per step:
         //   D += A B,  A(m, k) = x_k * (Kronecker prefix rows of k)(m),  B(k, :) = U_l row of k
         // with A = Ah + Al and B = Bh + Bl split into BF16 and D += Ah Bh + Ah Bl + Al Bh
         // in FP32 (the Al Bl term is below FP32 rounding of the sum).  B comes
-        // pre-split from Ulsplit; A is formed and split per 16 nonzeros into abuf.
-        // A rows of the 16 nonzeros k0 .. k0+15 into abuf: lane takes nonzero
-        // lane % 16 and half lane / 16 of its MZ entries
-        auto prep_a = [&](const unsigned char *st, int k0) {
-            const int el = lane & 15, h = lane >> 4;
-            const int q = k0 + el;
-            const int e = q & 31;
-            const float x = mval[q];
-            constexpr int HV = MZ / 2;
-            uint32_t hi[HV / 2], lo[HV / 2];
-            if (NM1 == 2) {
-                const float4 *src = reinterpret_cast<const float4 *>(st + soff(e, a.rb0, a.gs0)) + h * (HV / 4);
-#pragma unroll
-                for (int t = 0; t < HV / 4; ++t) {
-                    const float4 u = src[t];
-                    split2(__fmul2_rn(make_float2(u.x, u.y), make_float2(x, x)), hi[2 * t], lo[2 * t]);
-                    split2(__fmul2_rn(make_float2(u.z, u.w), make_float2(x, x)), hi[2 * t + 1], lo[2 * t + 1]);
-                }
-            } else {
-                // MZ = Ka * Kb with Kb = TL = 8: half h covers prefix index p in [h Ka/2, (h+1) Ka/2)
-                const float *ra = reinterpret_cast<const float *>(st + soff(e, a.rb0, a.gs0));
-                const float4 *rb = reinterpret_cast<const float4 *>(st + a.offb + soff(e, a.rb1, a.gs1));
-                const float4 b0 = rb[0], b1 = rb[1];
-#pragma unroll
-                for (int pp = 0; pp < HV / 8; ++pp) {
-                    const float xa = x * ra[h * (HV / 8) + pp];
-                    const float2 xx = make_float2(xa, xa);
-                    split2(__fmul2_rn(make_float2(b0.x, b0.y), xx), hi[4 * pp], lo[4 * pp]);
-                    split2(__fmul2_rn(make_float2(b0.z, b0.w), xx), hi[4 * pp + 1], lo[4 * pp + 1]);
-                    split2(__fmul2_rn(make_float2(b1.x, b1.y), xx), hi[4 * pp + 2], lo[4 * pp + 2]);
-                    split2(__fmul2_rn(make_float2(b1.z, b1.w), xx), hi[4 * pp + 3], lo[4 * pp + 3]);
-                }
-            }
-            uint4 *dh = reinterpret_cast<uint4 *>(abuf + soff(el, ARB, AGS) + h * HV * 2);
-            uint4 *dl = reinterpret_cast<uint4 *>(abuf + soff(el, ARB, AGS) + MZ * 2 + h * HV * 2);
-#pragma unroll
-            for (int t = 0; t < HV / 8; ++t) {
-                dh[t] = make_uint4(hi[4 * t], hi[4 * t + 1], hi[4 * t + 2], hi[4 * t + 3]);
-                dl[t] = make_uint4(lo[4 * t], lo[4 * t + 1], lo[4 * t + 2], lo[4 * t + 3]);
-            }
-        };
-        // D += contributions of window nonzeros [qa, qb) (one row); k-steps of 16
+        // pre-split from Ulsplit (hi row, then lo row); A is formed and split in
+        // registers.  Lane (gq, tq) holds A(gq (+8), k) and B(k, gq) of the
+        // nonzeros k = 2tq, 2tq+1, 2tq+8, 2tq+9 of the step (the mma fragments).
         auto mma_accumulate = [&](int qa, int qb) {
-            if constexpr (MT > 0) {
-                const int lm = lane >> 3, lr = lane & 7;  // ldmatrix: matrix lm, row lr
-                const int tq = lane & 3;
-                int k0 = qa & ~15;
-                while (k0 < qb) {
-                    const int s = k0 >> 5;
-                    need_stage(s);
-                    const unsigned char *st = ring + (size_t)((gst + s) & (a.nb - 1)) * a.stage_bytes;
-                    const unsigned char *stl = st + (NM1 == 2 ? a.offb : a.offc);
-                    const int rbl = NM1 == 2 ? a.rb1 : a.rb2, gsl = NM1 == 2 ? a.gs1 : a.gs2;
-                    const int kend = min(qb, (s + 1) << 5);
-                    for (; k0 < kend; k0 += 16) {
-                        prep_a(st, k0);
-                        __syncwarp();
-                        // A fragments: matrices (k 0-7 | 8-15) x (m 0-7 | 8-15) of m-tile mt
-                        uint32_t ah[MT][4], al[MT][4];
+            if constexpr (MMA) {
+                const int gq = lane >> 2, tq = lane & 3;
+                const uint16_t *Bs = reinterpret_cast<const uint16_t *>(a.Ulsplit);
+                for (int k0 = qa & ~15; k0 < qb; k0 += 16) {
+                    float av[4][MT][2];
+                    uint32_t hb[4][NT], lb[4][NT];
 #pragma unroll
-                        for (int mt = 0; mt < MT; ++mt) {
-                            const unsigned char *pa =
-                                abuf + soff(lr + 8 * (lm >> 1), ARB, AGS) + (mt * 16 + 8 * (lm & 1)) * 2;
-                            ldsm_x4_t(ah[mt], pa);
-                            ldsm_x4_t(al[mt], pa + MZ * 2);
-                        }
-                        // B fragments from the staged split rows (row = nonzero k, n contiguous)
-                        const unsigned char *rowk = stl + soff((k0 & 31) + lr + 8 * (lm & 1), rbl, gsl);
-                        uint32_t bh[NT][2], bl[NT][2];
-                        if (NT == 1) {
-                            uint32_t r4[4];
-                            ldsm_x4_t(r4, rowk + (lm >> 1) * 8 * 2);  // matrices 2, 3: lo half of the row
-                            bh[0][0] = r4[0];
-                            bh[0][1] = r4[1];
-                            bl[0][0] = r4[2];
-                            bl[0][1] = r4[3];
-                        } else {
-#pragma unroll
-                            for (int np = 0; np < NT / 2; ++np) {
-                                uint32_t r4[4];
-                                ldsm_x4_t(r4, rowk + (np * 16 + 8 * (lm >> 1)) * 2);
-                                bh[2 * np][0] = r4[0];
-                                bh[2 * np][1] = r4[1];
-                                bh[2 * np + 1][0] = r4[2];
-                                bh[2 * np + 1][1] = r4[3];
-                                ldsm_x4_t(r4, rowk + (a.Kl + np * 16 + 8 * (lm >> 1)) * 2);
-                                bl[2 * np][0] = r4[0];
-                                bl[2 * np][1] = r4[1];
-                                bl[2 * np + 1][0] = r4[2];
-                                bl[2 * np + 1][1] = r4[3];
-                            }
-                        }
-                        if (k0 < qa || k0 + 16 > kend) {
-                            // nonzeros outside [qa, kend): zero their A and B entries (stale
-                            // staging may hold any bit pattern)
-                            auto ok_k = [&](int k) { return k0 + k >= qa && k0 + k < kend; };
-                            const uint32_t m01 = (ok_k(2 * tq) ? 0xFFFFu : 0u) | (ok_k(2 * tq + 1) ? 0xFFFF0000u : 0u);
-                            const uint32_t m89 =
-                                (ok_k(2 * tq + 8) ? 0xFFFFu : 0u) | (ok_k(2 * tq + 9) ? 0xFFFF0000u : 0u);
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        const int kq = k0 + 2 * tq + (q4 & 1) + 8 * (q4 >> 1);
+                        const bool valid = kq >= qa && kq < qb;
+                        const float x = valid ? mval[kq] : 0.f;
+                        const int32_t ra = valid ? mia[kq] : 0;
+                        const int32_t rl = valid ? (NM1 == 2 ? mib[kq] : mic[kq]) : 0;
+                        if (NM1 == 2) {
+                            // A(m, k) = x * Ua(row, m), m = mt*16 + gq (+8)
 #pragma unroll
                             for (int mt = 0; mt < MT; ++mt) {
-                                ah[mt][0] &= m01;
-                                ah[mt][1] &= m01;
-                                ah[mt][2] &= m89;
-                                ah[mt][3] &= m89;
-                                al[mt][0] &= m01;
-                                al[mt][1] &= m01;
-                                al[mt][2] &= m89;
-                                al[mt][3] &= m89;
+                                av[q4][mt][0] = x * __ldg(a.Ua + (size_t)ra * a.Kr0 + mt * 16 + gq);
+                                av[q4][mt][1] = x * __ldg(a.Ua + (size_t)ra * a.Kr0 + mt * 16 + gq + 8);
                             }
+                        } else {
+                            // Ka = Kb = 8: m = p*8 + r, so rows m = mt*16 + gq (+8) are p = 2mt (+1), r = gq
+                            const int32_t rb = valid ? mib[kq] : 0;
+                            const float xb = x * __ldg(a.Ub + (size_t)rb * 8 + gq);
 #pragma unroll
-                            for (int nt = 0; nt < NT; ++nt) {
-                                bh[nt][0] &= m01;
-                                bh[nt][1] &= m89;
-                                bl[nt][0] &= m01;
-                                bl[nt][1] &= m89;
+                            for (int mt = 0; mt < MT; ++mt) {
+                                av[q4][mt][0] = xb * __ldg(a.Ua + (size_t)ra * 8 + 2 * mt);
+                                av[q4][mt][1] = xb * __ldg(a.Ua + (size_t)ra * 8 + 2 * mt + 1);
                             }
                         }
+                        const uint16_t *brow = Bs + (size_t)rl * 2 * a.Kl;
 #pragma unroll
-                        for (int mt = 0; mt < MT; ++mt)
-#pragma unroll
-                            for (int nt = 0; nt < NT; ++nt) {
-                                mma_bf16(dtmp[mt][nt], al[mt], bh[nt][0], bh[nt][1]);
-                                mma_bf16(dtmp[mt][nt], ah[mt], bl[nt][0], bl[nt][1]);
-                                mma_bf16(dtmp[mt][nt], ah[mt], bh[nt][0], bh[nt][1]);
-                            }
-                        if (++ksteps == KS_FLUSH) flush_d();
-                        __syncwarp();  // abuf is rewritten by the next k-step
+                        for (int nt = 0; nt < NT; ++nt) {
+                            hb[q4][nt] = valid ? __ldg(brow + nt * 8 + gq) : 0u;
+                            lb[q4][nt] = valid ? __ldg(brow + a.Kl + nt * 8 + gq) : 0u;
+                        }
                     }
+#pragma unroll
+                    for (int mt = 0; mt < MT; ++mt) {
+                        uint32_t ah[4], al[4];
+                        split2(make_float2(av[0][mt][0], av[1][mt][0]), ah[0], al[0]);
+                        split2(make_float2(av[0][mt][1], av[1][mt][1]), ah[1], al[1]);
+                        split2(make_float2(av[2][mt][0], av[3][mt][0]), ah[2], al[2]);
+                        split2(make_float2(av[2][mt][1], av[3][mt][1]), ah[3], al[3]);
+#pragma unroll
+                        for (int nt = 0; nt < NT; ++nt) {
+                            const uint32_t bh0 = hb[0][nt] | (hb[1][nt] << 16), bh1 = hb[2][nt] | (hb[3][nt] << 16);
+                            const uint32_t bl0 = lb[0][nt] | (lb[1][nt] << 16), bl1 = lb[2][nt] | (lb[3][nt] << 16);
+                            mma_bf16(dtmp[mt][nt], al, bh0, bh1);
+                            mma_bf16(dtmp[mt][nt], ah, bl0, bl1);
+                            mma_bf16(dtmp[mt][nt], ah, bh0, bh1);
+                        }
+                    }
+                    if (++ksteps == KS_FLUSH) flush_d();
                 }
             }
         };
 
-        if (MT > 0 && it < a.nitem_long) {
-            // ---------------- long rows on the tensor cores: the whole warp owns the
-            // row's tile; carries across windows and items as in the FMA path below
+        if (PART == 0) {
+            // ---------------- long rows; a row that runs into the next item of
+            // the same range carries its partial tile over
             if (W0.first && !carry) {
                 j = a.item_aux[it];
-                zero_d();
-            }
-            carry = false;
-            int64_t pos = p0;
-            while (pos < p1) {
-                if (jc != j) {
-                    jc = j;
-                    crs = a.lrp[j];
-                    cre = a.lrp[j + 1];
-                }
-                const int64_t rs = crs, re = cre;
-                const int64_t a1 = min(re, p1);
-                if (a1 <= pos) break;
-                mma_accumulate((int)(pos - p0), (int)(a1 - p0));
-                const bool row_end = (a1 == re);
-                const bool item_end = (a1 == te);
-                if (!row_end && item_end && it + 1 < r1) {
-                    carry = true;
-                } else if (row_end || item_end) {
-                    const int32_t r = a.lrow[j];
-                    const bool full = (rs >= lbeg) && (re <= lend);
-                    const int slot = (j == lfirst) ? 0 : 1;
-                    store_d(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (rg * 2 + slot) * a.Pm);
-                    zero_d();
-                    if (row_end) ++j;
-                }
-                pos = a1;
-            }
-        } else if (it < a.nitem_long) {
-            // ---------------- long rows: groups split a row's nonzeros; a row that
-            // runs into the next item of the same range carries its partial y over
-            if (W0.first && !carry) {
-                j = a.item_aux[it];
-                zero_y();
+                if (MMA) zero_d(); else zero_y();
             }
             carry = false;
             int64_t pos = p0;
@@ -681,27 +464,35 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 const int64_t rs = crs, re = cre;
                 const int64_t a1 = min(re, p1);
                 if (a1 <= pos) break;  // descriptors always advance; never spin on bad input
-                accumulate((int)(pos - p0), (int)(a1 - p0), false);
+                if (MMA) mma_accumulate((int)(pos - p0), (int)(a1 - p0));
+                else accumulate((int)(pos - p0), (int)(a1 - p0), false);
                 const bool row_end = (a1 == re);
                 const bool item_end = (a1 == te);
                 if (!row_end && item_end && it + 1 < r1) {
                     carry = true;  // same row continues in the next item of this range
                 } else if (row_end || item_end) {
-                    __syncwarp();
-                    for (int o = lpn; o < 32; o <<= 1) {
-#pragma unroll
-                        for (int jj = 0; jj < TL; ++jj)
-#pragma unroll
-                            for (int kk = 0; kk < TV / 2; ++kk) {
-                                y2[jj][kk].x += __shfl_xor_sync(0xffffffffu, y2[jj][kk].x, o);
-                                y2[jj][kk].y += __shfl_xor_sync(0xffffffffu, y2[jj][kk].y, o);
-                            }
-                    }
                     const int32_t r = a.lrow[j];
                     const bool full = (rs >= lbeg) && (re <= lend);
                     const int slot = (j == lfirst) ? 0 : 1;
-                    if (g == 0) store_tile(full ? a.Y + (int64_t)r * a.Pm : a.ypart + (rg * 2 + slot) * a.Pm);
-                    zero_y();
+                    float *dst = full ? a.Y + (int64_t)r * a.Pm : a.ypart + (rg * 2 + slot) * a.Pm;
+                    if (MMA) {
+                        store_d(dst);
+                        zero_d();
+                    } else {
+                        // lane groups split the row's nonzeros: add their tiles
+                        __syncwarp();
+                        for (int o = lpn; o < 32; o <<= 1) {
+#pragma unroll
+                            for (int jj = 0; jj < TLs; ++jj)
+#pragma unroll
+                                for (int kk = 0; kk < TVs / 2; ++kk) {
+                                    y2[jj][kk].x += __shfl_xor_sync(0xffffffffu, y2[jj][kk].x, o);
+                                    y2[jj][kk].y += __shfl_xor_sync(0xffffffffu, y2[jj][kk].y, o);
+                                }
+                        }
+                        if (g == 0) store_tile(dst);
+                        zero_y();
+                    }
                     if (row_end) ++j;
                 }
                 pos = a1;
@@ -724,7 +515,6 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 if (a1 <= pos) break;
                 accumulate((int)(pos - p0), (int)(a1 - p0), true);
                 if (a1 == se) {
-                    __syncwarp();
                     const int32_t r = a.srow[j * NG + g];
                     if (r >= 0) store_tile(a.Y + (int64_t)r * a.Pm);
                     zero_y();
@@ -733,11 +523,7 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
                 pos = a1;
             }
         }
-        // stages issued but not consumed (none: every stage of the window is waited for)
-        need_stage(nst - 1);
-        __syncwarp();
-        gst += nst;
-        pre = pre_next;
+        __syncwarp();  // every lane is done with window mk's buffer before it is refilled
         W0 = W1;
         W1 = W2;
         const int bt = b0;
@@ -745,14 +531,12 @@ __global__ void __launch_bounds__(HY_WARPS * 32) k_hyb(HybArgs a) {
         b1 = b2;
         b2 = bt;
         ++mk;
-        if (!ok) break;
     }
     if (!ok) {
-        // a staged copy never completed: bounded waits for this warp's requested
+        // a window's copy never completed: bounded waits for this warp's requested
         // windows that were not consumed, then leave
         for (int wq = mk; wq < issued; ++wq) mbar_wait(mbar + wq % 3, (uint32_t)((wq / 3) & 1), nullptr);
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // Y rows of the long rows cut by warp-range boundaries.  Piece of range t0
@@ -910,8 +694,7 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
 
 struct HybLaunch {
     size_t smem = 0;
-    int bar_off = 0, gs_off = 0, w_off = 0, w_stride = 0, meta_bytes = 0, ring_off = 0, stage_bytes = 0;
-    int nb = HY_NB, rb0 = 0, rb1 = 0, rb2 = 0, gs0 = 0, gs1 = 0, gs2 = 0, offb = 0, offc = 0, abuf_off = 0;
+    int bar_off = 0, gs_off = 0, w_off = 0, w_stride = 0, meta_bytes = 0;
     int MT = 0, NT = 0;  // tensor-core tiles of the long rows (0: FP32 FMA tiles)
 };
 
@@ -942,37 +725,14 @@ void mix_shape(const hoqri_ctx *c, int n, const FastTile &p, int *MT, int *NT) {
 HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p) {
     HybLaunch L;
     const int narr = p.nm1 + 1;
-    // ranks of the gathered rows: (Ua, Ub[, Uc]) = other modes in ascending order
-    int K3[3] = {0, 0, 0}, j = 0;
-    for (int m = 0; m < c->N; ++m)
-        if (m != n) K3[j++] = c->K[m];
     mix_shape(c, n, p, &L.MT, &L.NT);
-    // staged rows: 16 pad bytes after each 128 bytes of rows (soff)
-    auto gsh = [](int K) { return K >= 32 ? 0 : (K == 16 ? 1 : (K == 8 ? 2 : 3)); };
-    auto region = [&](int K) { return 32 * 4 * K + (32 >> gsh(K)) * 16; };
-    L.rb0 = 4 * K3[0];
-    L.rb1 = 4 * K3[1];
-    L.rb2 = p.nm1 == 3 ? 4 * K3[2] : 0;
-    L.gs0 = gsh(K3[0]);
-    L.gs1 = gsh(K3[1]);
-    L.gs2 = p.nm1 == 3 ? gsh(K3[2]) : 0;
-    L.offb = region(K3[0]);
-    L.offc = L.offb + region(K3[1]);
-    L.stage_bytes = al128(L.offc + (p.nm1 == 3 ? region(K3[2]) : 0));
+    // shared memory: three index/value windows per warp and their barriers
     L.meta_bytes = HY_WB * 4;
     L.bar_off = 0;
-    L.gs_off = al128(HY_WARPS * (3 + HY_NB) * 8);
+    L.gs_off = al128(HY_WARPS * 3 * 8);
     L.w_off = L.gs_off;
-    L.ring_off = al128(3 * narr * L.meta_bytes);
-    const int abuf_bytes = L.MT > 0 ? al128(16 * 64 * L.MT + (L.MT == 1 ? 8 : 16) * 16) : 0;
-    // four stages in flight per warp, two when four do not fit (wide rows)
-    for (L.nb = HY_NB; L.nb >= 2; L.nb /= 2) {
-        L.abuf_off = al128(L.ring_off + L.nb * L.stage_bytes);
-        L.w_stride = al128(L.abuf_off + abuf_bytes);
-        L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
-        if (L.smem <= HY_SMEM_CAP) break;
-    }
-    if (L.nb < 2) L.nb = 2;
+    L.w_stride = al128(3 * narr * L.meta_bytes);
+    L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
     return L;
 }
 
@@ -992,13 +752,22 @@ __global__ void k_split_bf16(const float *U, int64_t rows, int K, uint32_t *out)
 
 template <int NM1>
 hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, const HybLaunch &L) {
+    // two blocks of HY_WARPS warps per SM: part 0 (long rows), then part 1 (slices)
+    const int grid = HY_BLOCKS_PER_SM * c->num_sms;
 #define HQ_HYB(TLV, TVV, MTV, NTV)                                                                           \
     if (p.TL == TLV && p.TV == TVV && L.MT == MTV && L.NT == NTV) {                                          \
-        auto kern = k_hyb<NM1, TLV, TVV, MTV, NTV>;                                                          \
-        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));      \
-        const int grid = c->num_sms;                                                                         \
-        kern<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                                 \
-        c->nlaunch++;                                                                                        \
+        auto k0 = k_hyb<NM1, TLV, TVV, MTV, NTV, 0>;                                                         \
+        auto k1 = k_hyb<NM1, TLV, TVV, 0, 0, 1>;                                                             \
+        HQ_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
+        HQ_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
+        if (a.nitem_long > 0) {                                                                              \
+            k0<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                               \
+            c->nlaunch++;                                                                                    \
+        }                                                                                                    \
+        if (a.nitem > a.nitem_long) {                                                                        \
+            k1<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                               \
+            c->nlaunch++;                                                                                    \
+        }                                                                                                    \
         HQ_CUDA(cudaGetLastError());                                                                         \
         return HOQRI_OK;                                                                                     \
     }
@@ -1067,19 +836,6 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.w_off = L.w_off;
     a.w_stride = L.w_stride;
     a.meta_bytes = L.meta_bytes;
-    a.ring_off = L.ring_off;
-    a.stage_bytes = L.stage_bytes;
-    a.nb = L.nb;
-    a.lgnb = L.nb == 4 ? 2 : 1;
-    a.rb0 = L.rb0;
-    a.rb1 = L.rb1;
-    a.rb2 = L.rb2;
-    a.gs0 = L.gs0;
-    a.gs1 = L.gs1;
-    a.gs2 = L.gs2;
-    a.offb = L.offb;
-    a.offc = L.offc;
-    a.abuf_off = L.abuf_off;
     {
         int j = 0;
         const float *Uo[3] = {nullptr, nullptr, nullptr};

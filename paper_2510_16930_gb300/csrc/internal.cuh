@@ -13,6 +13,9 @@
 
 #define HOQRI_MAXN 8
 #define HOQRI_MAXK 64
+// blocks of the hybrid pass kernel per SM (8 warps each); the work ranges of
+// its long rows are cut for HY_BLOCKS_PER_SM * 8 warps per SM
+#define HY_BLOCKS_PER_SM 2
 
 namespace hoqri {
 

@@ -500,11 +500,11 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
         ia.push_back((int32_t)j);
         j = k;
     }
-    // long items: contiguous ranges, one per warp of a fixed grid (8 warps per SM),
+    // long items: contiguous ranges, one per warp of the pass's fixed grid,
     // so a long row crossing items inside a range carries its partial sum; a long
     // row crossing a range boundary is completed from per-range pieces.  Slice
     // items are dealt to the warps in turn.
-    const int64_t W = (int64_t)c->num_sms * 8;
+    const int64_t W = (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8;
     const int64_t ipw = std::max<int64_t>(1, (nitem_long + W - 1) / W);
     const int64_t nrange = std::max<int64_t>(1, (nitem_long + ipw - 1) / ipw);
     for (int64_t jj = 0; jj < nlong; ++jj) {
