@@ -47,6 +47,7 @@ def parse():
                     help="arithmetic of the run (default: the workload's own)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP32 comparison")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -182,17 +183,18 @@ def cpu_oracle_rate(X, U0, target_s, max_sample=None):
         oracle.hoqri(X.dims, idx, v, U0, 1)
         return time.perf_counter() - t0
 
-    S = min(2000, X.nnz)
-    t = run(S)
-    while t < 0.5 and S < X.nnz:
-        S = min(X.nnz, S * 4)
-        t = run(S)
-    S2 = int(min(X.nnz, max(S, S * target_s / max(t, 1e-3) * 0.8)))
+    # a sweep costs a fixed part (the QR of every factor) plus a part per
+    # nonzero: two calibration runs give both, then S is sized for target_s
+    S1 = min(2000, X.nnz)
+    t1 = run(S1)
+    S2 = min(X.nnz, 8 * S1)
+    t2 = run(S2)
+    slope = max((t2 - t1) / max(S2 - S1, 1), 1e-9)
+    fixed = max(t1 - slope * S1, 0.0)
+    S = int(min(X.nnz, max(S2, (target_s - fixed) / slope)))
     if max_sample:
-        S2 = min(S2, max_sample)
-    if S2 != S:
-        t = run(S2)
-        S = S2
+        S = min(S, max_sample)
+    t = run(S) if S != S2 else t2
     return S * N / t, oracle.threads(), f"first {S} of {X.nnz} nonzeros, one sweep (N={N} modes), FP64", t
 
 
@@ -239,6 +241,82 @@ def config_block(args, cfg, X, nnz_c):
             "parallelism": f"replicas x{args.gpus}"}
 
 
+def stream_roofline(X, cfg, rows, nnz, prof, prec, peaks, nsm, cfg_name):
+    """Roofline entry of the nonzero-stream kernel, per launch (one per mode and
+    pass).  Algorithmic flops: 2 * nnz * P_{-n} (the multiply-add of every
+    Kronecker entry into y_i); algorithmic bytes: the stream (N-1 int32 indices
+    and an FP32 value per nonzero) plus the R_n x P_{-n} FP32 rows of Y written."""
+    from paper_2510_16930_gb300 import hoqri
+    N = X.N
+    ranks = cfg["ranks"]
+    P = math.prod(ranks)
+    flops = sum(2.0 * nnz * (P // ranks[n]) for n in range(N)) / N
+    byts = sum(nnz * (4 * (N - 1) + 4) + rows[n] * (P // ranks[n]) * 4 for n in range(N)) / N
+    n_l = max(prof.get("stream_n", 0), 1)
+    ms = prof.get("stream_ms", 0.0) / n_l
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == hoqri.HOQRI_BF16X3:
+        # three BF16 products per Kronecker entry on the tensor cores (long rows)
+        bound, unit, alg = "tensor", "TFLOP/s", 3.0 * flops
+        peak = float(peaks.get("bf16_tflops", 1900.0))
+        src = "measured bf16 burst (MEASURED_PEAKS.json)" if "bf16_tflops" in peaks else "fallback 1.9 PFLOP/s"
+    else:
+        bound, unit, alg = "alu", "TFLOP/s", flops
+        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        src = f"derived: {nsm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz"
+    achieved = alg / (ms / 1e3) / 1e12 if ms > 0 else None
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": ncu_traffic(cfg_name, "k_hyb"), "kernel": "k_hyb (nonzero-stream pass, long rows + slices)",
+            "peak_source": src, "alg_flops_per_launch": alg, "alg_bytes_per_launch": byts,
+            "hbm_gbs_achieved": byts / (ms / 1e3) / 1e9 if ms > 0 else None,
+            "hbm_gbs_peak_measured": peaks.get("hbm_gbs"), "ms_per_launch": ms,
+            "ttmctc_ms_per_mode": prof["ttmctc_ms"] / max(prof["ttmctc_n"], 1),
+            "core_ms_per_mode": prof["core_ms"] / max(prof["core_n"], 1),
+            "qr_ms_per_mode": prof["qr_ms"] / max(prof["qr_n"], 1)}
+
+
+def timed_sweeps(hoqri, torch, ctx, stream, steps, warmup):
+    """warm-up sweeps, then `steps` sweeps between CUDA events on the context stream"""
+    hoqri.hoqri_iterate(ctx, warmup, want_hist=False)
+    hoqri.hoqri_synchronize(ctx)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    hoqri.hoqri_iterate(ctx, steps, want_hist=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def mixed_vs_plain(hoqri, torch, X, U0, cfg, stream, steps, warmup, fit_iters=3):
+    """The split-BF16 form against the plain FP32 method on the same workload:
+    sweep throughput of both, and the relative error of the residual after
+    fit_iters sweeps from the same initial factors against the FP64 path."""
+    import numpy as np
+    N = X.N
+    res = {}
+    hist = {}
+    for name, prec in (("fp64", hoqri.HOQRI_FP64), ("fp32", hoqri.HOQRI_FP32), ("bf16x3", hoqri.HOQRI_BF16X3)):
+        dt = np.float64 if prec == hoqri.HOQRI_FP64 else np.float32
+        idx_d = [torch.from_numpy(a).cuda() for a in X.idx]
+        vals_d = torch.from_numpy(X.vals.astype(dt)).cuda()
+        U_d = [torch.from_numpy(u.astype(dt)).cuda() for u in U0]
+        opt = hoqri.hoqri_default_options(prec=prec)
+        c = hoqri.hoqri_create(X.dims, cfg["ranks"], X.nnz, idx_d, vals_d, opt, U_d, stream.cuda_stream)
+        del idx_d, vals_d
+        hist[name] = hoqri.hoqri_iterate(c, fit_iters)
+        if prec != hoqri.HOQRI_FP64:
+            nnz_c, _, _ = hoqri.hoqri_info(c, N)
+            ms = timed_sweeps(hoqri, torch, c, stream, steps, warmup)
+            res[name] = {"value": nnz_c * N * steps / (ms / 1e3), "ms_per_step": ms / steps}
+        hoqri.hoqri_destroy(c)
+    for name in ("fp32", "bf16x3"):
+        res[name]["fit_rel_err_vs_fp64"] = float(np.max(np.abs(hist[name] - hist["fp64"]) / hist["fp64"]))
+    res["fit_sweeps"] = fit_iters
+    res["speedup_bf16x3_over_fp32"] = res["bf16x3"]["value"] / res["fp32"]["value"]
+    return res
+
+
 # ---------------------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -277,7 +355,6 @@ def run_ours(args):
     except Exception:
         pass
     clocks = ClockSampler(uuid)
-    hoqri.hoqri_profile_enable(ctx, True)
     _, launches0 = hoqri.hoqri_profile_read(ctx)
     clocks.start()
     if world > 1:
@@ -285,16 +362,21 @@ def run_ours(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    hist = hoqri.hoqri_iterate(ctx, args.steps, want_hist=False)
+    hoqri.hoqri_iterate(ctx, args.steps, want_hist=False)  # sweeps replay a captured CUDA graph
     e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    prof, launches1 = hoqri.hoqri_profile_read(ctx)
-    hoqri.hoqri_profile_enable(ctx, False)
+    _, launches1 = hoqri.hoqri_profile_read(ctx)
     resid_last, _, _ = hoqri.hoqri_fit(ctx)
+    # per-kernel timing: a few more sweeps with the library's CUDA-event tracing
+    # (plain launches; kept out of the timed region above)
+    hoqri.hoqri_profile_enable(ctx, True)
+    hoqri.hoqri_iterate(ctx, min(args.steps, 5), want_hist=False)
+    prof, _ = hoqri.hoqri_profile_read(ctx)
+    hoqri.hoqri_profile_enable(ctx, False)
     ms_max = ms
     if world > 1:
         t = torch.tensor([ms], device="cuda")
@@ -302,39 +384,15 @@ def run_ours(args):
         ms_max = float(t.item())
     value = nnz_c * N * args.steps * world / (ms_max / 1e3)
 
-    # roofline of the dominant kernel (the TTMcTC pass), per launch
+    # roofline of the dominant kernel: the pass over a mode's nonzero stream
+    # (k_hyb, long-row and slice launches), timed by its own CUDA events
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    flops = [alg_flops_per_pass(X.dims, cfg["ranks"], rows, nnz_c, n) for n in range(N)]
-    byts = [alg_bytes_per_pass(X.dims, cfg["ranks"], rows, nnz_c, n, rsize) for n in range(N)]
-    ttm_launches = max(prof["ttmctc_n"], 1)
-    ttm_ms = prof["ttmctc_ms"] / ttm_launches
-    core_ms = prof["core_ms"] / max(prof["core_n"], 1)
-    flops_per_launch = sum(flops) / N
-    bytes_per_launch = sum(byts) / N
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    nsm = torch.cuda.get_device_properties(local).multi_processor_count
-    if prec == hoqri.HOQRI_FP64:
-        bound, unit = "alu", "TFLOP/s"
-        peak = None  # FP64 rate: derived below from the measured clock
-        achieved = flops_per_launch / (ttm_ms / 1e3) / 1e12
-        peak = nsm * 2 * 2 * sm_max * 1e6 / 1e12  # assumed 2 FP64 FMA/clk/SM
-    else:
-        bound, unit = "alu", "TFLOP/s"
-        achieved = flops_per_launch / (ttm_ms / 1e3) / 1e12
-        peak = nsm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    traffic = ncu_traffic(args.config, "ttmctc")
-    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": traffic, "kernel": "TTMcTC pass (k_pass_*)",
-                "peak_source": f"derived: {nsm} SMs x {FP32_LANES_PER_SM if prec != 0 else 2} lanes x 2 flop x {sm_max:.0f} MHz",
-                "hbm_gbs_achieved": bytes_per_launch / (ttm_ms / 1e3) / 1e9,
-                "hbm_gbs_peak_measured": peaks.get("hbm_gbs"),
-                "alg_flops_per_launch": flops_per_launch, "alg_bytes_per_launch": bytes_per_launch,
-                "ms_per_launch": ttm_ms, "core_pass_ms_per_launch": core_ms,
-                "qr_ms_per_launch": prof["qr_ms"] / max(prof["qr_n"], 1)}
+    roofline = stream_roofline(X, cfg, rows, nnz_c, prof, prec, peaks,
+                               torch.cuda.get_device_properties(local).multi_processor_count, args.config)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -343,6 +401,8 @@ def run_ours(args):
            "data": "synthetic", "config": config_block(args, cfg, X, nnz_c), "roofline": roofline,
            "gpu_launches": int(launches1 - launches0), "clocks": clk,
            "final_resid": resid_last, "device_bytes": dev_bytes}
+    if rank == 0 and world == 1 and not args.no_mixed and prec != hoqri.HOQRI_FP64:
+        out["mixed_vs_fp32"] = mixed_vs_plain(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup)
 
     # end to end through the public API from pinned host buffers
     if not args.no_e2e:

@@ -68,6 +68,10 @@ static hoqri_status ensure_slots(hoqri_ctx *c, int64_t slots) {
     }
     c->dnorm = nd;
     c->dnorm_slots = slots;
+    if (c->sweep_exec) {  // the captured sweep writes into the old history array
+        cudaGraphExecDestroy(c->sweep_exec);
+        c->sweep_exec = nullptr;
+    }
     return HOQRI_OK;
 }
 
@@ -102,6 +106,8 @@ static void destroy_impl(hoqri_ctx *c) {
         dfree(M.span);
         dfree(c->U[n]);
     }
+    dfree(c->gslot);
+    dfree(c->gcount);
     dfree(c->G);
     dfree(c->A);
     dfree(c->dnorm);
@@ -498,6 +504,68 @@ hoqri_status hoqri_orthonormalize_noalloc(int32_t prec, int64_t I, int32_t K, co
     return orthonormalize_noalloc(prec, I, K, A_in, U_out, static_cast<cudaStream_t>(stream));
 }
 
+namespace hoqri {
+
+// One sweep of Alg. 2 (every block update once); slots[n] receives ||G||^2
+// after the update of block n.
+static hoqri_status sweep(hoqri_ctx *c, double *slots) {
+    for (int n = 0; n < c->N; ++n) {
+        const bool one = hyb_mode(c, n);
+        HQ_TRY(ttmctc_block(c, n, c->A, one));
+        HQ_TRY(orthonormalize(c, n, c->A, c->U[n]));
+        if (one) HQ_TRY(core_from_y(c, n, slots + n));
+        else HQ_TRY(refresh_core(c, (n + 1) % c->N, slots + n));
+    }
+    return HOQRI_OK;
+}
+
+// appends the N norms of the replayed sweep to the history: sweep t = *count
+__global__ void k_hist_push(const double *slots, int N, double *hist, int32_t *count) {
+    const int t = *count;
+    for (int n = 0; n < N; ++n) hist[(int64_t)t * N + n] = slots[n];
+    *count = t + 1;
+}
+
+// Captures one sweep (plus the history append) into a CUDA graph; on any
+// capture failure the context falls back to plain launches.
+static hoqri_status capture_sweep(hoqri_ctx *c) {
+    if (!c->gslot) HQ_TRY(dalloc(c, (void **)&c->gslot, c->N * sizeof(double)));
+    if (!c->gcount) HQ_TRY(dalloc(c, (void **)&c->gcount, sizeof(int32_t)));
+    const int64_t l0 = c->nlaunch;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->sweep_graph_off = true;
+        return HOQRI_OK;
+    }
+    hoqri_status s = sweep(c, c->gslot);
+    if (s == HOQRI_OK) {
+        k_hist_push<<<1, 1, 0, c->stream>>>(c->gslot, c->N, c->dnorm + 3, c->gcount);
+        c->nlaunch++;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (s != HOQRI_OK || e != cudaSuccess || !g) {
+        cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        c->nlaunch = l0;
+        c->sweep_graph_off = true;
+        g_last_error.clear();
+        return HOQRI_OK;
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->sweep_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        c->sweep_exec = nullptr;
+        c->sweep_graph_off = true;
+    }
+    c->sweep_launches = c->nlaunch - l0;
+    c->nlaunch = l0;
+    return HOQRI_OK;
+}
+
+}  // namespace hoqri
+
 hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
     g_last_error.clear();
     HQ_TRY(check_mode(c, 0));
@@ -514,15 +582,18 @@ hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
     }
     // slot 2 + k holds ||G||^2 after k block updates (k = 0: the initial core)
     HQ_TRY(refresh_core(c, 0, c->dnorm + 2));
-    for (int t = 0; t < iters; ++t) {
-        for (int n = 0; n < N; ++n) {
-            double *slot = c->dnorm + 2 + (int64_t)t * N + n + 1;
-            const bool one = hyb_mode(c, n);
-            HQ_TRY(ttmctc_block(c, n, c->A, one));
-            HQ_TRY(orthonormalize(c, n, c->A, c->U[n]));
-            if (one) HQ_TRY(core_from_y(c, n, slot));
-            else HQ_TRY(refresh_core(c, (n + 1) % N, slot));
+    // sweeps replay one captured CUDA graph, unless tracing is on (its events
+    // are recorded per call on the host side) or capture is unavailable
+    const bool graphs = c->opt.use_graphs && !c->profiling && iters > 0 && !c->sweep_graph_off;
+    if (graphs && !c->sweep_exec) HQ_TRY(capture_sweep(c));
+    if (graphs && c->sweep_exec) {
+        HQ_CUDA(cudaMemsetAsync(c->gcount, 0, sizeof(int32_t), c->stream));
+        for (int t = 0; t < iters; ++t) {
+            HQ_CUDA(cudaGraphLaunch(c->sweep_exec, c->stream));
+            c->nlaunch += c->sweep_launches;
         }
+    } else {
+        for (int t = 0; t < iters; ++t) HQ_TRY(sweep(c, c->dnorm + 2 + (int64_t)t * N + 1));
     }
     if (resid_hist || c->opt.qr_kind == 2) {
         std::vector<double> h(2 + (size_t)iters * N + 1);

@@ -137,7 +137,11 @@ struct hoqri_ctx {
     int pass_grid_fast = 0;
     int64_t device_bytes = 0;
     // CUDA graph of one sweep
-    cudaGraphExec_t sweep_exec = nullptr;
+    cudaGraphExec_t sweep_exec = nullptr;  // one captured sweep (use_graphs)
+    int64_t sweep_launches = 0;             // kernels in the captured sweep
+    bool sweep_graph_off = false;           // capture failed once: plain launches from then on
+    double *gslot = nullptr;                // ||G||^2 after each block update of the captured sweep
+    int32_t *gcount = nullptr;              // sweeps replayed since the history base
     int graph_slot_base = -1;
     double host_norm[2] = {0, 0};
     // tracing

@@ -324,6 +324,8 @@ __global__ void k_gauss(T *out, int64_t n, uint64_t seed, uint32_t stream_id) {
     }
 }
 
+__global__ void k_set_flag(int32_t *flag, int32_t v) { *flag = v; }
+
 // one Gram block per SM at most (the FP64 multiply-adds need every SM; fewer
 // partials keep the Cholesky's reduction short)
 int gram_blocks(int64_t I, int num_sms) {
@@ -341,12 +343,10 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     const int npairs = K * (K + 1) / 2;
     double *Rinv = c->qr_small;
     const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
-    if (c->opt.qr_kind == 1) {
-        int32_t one = 1;
-        HQ_CUDA(cudaMemcpyAsync(c->dflag, &one, sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    } else {
-        HQ_CUDA(cudaMemsetAsync(c->dflag, 0, sizeof(int32_t), st));
-    }
+    // flag 0: CholeskyQR2; flag 1 (qr_kind 1): Householder from the start.  Set
+    // with a kernel, not a copy from host memory, so a captured graph replays it.
+    k_set_flag<<<1, 1, 0, st>>>(c->dflag, c->opt.qr_kind == 1 ? 1 : 0);
+    c->nlaunch++;
     for (int pass = 0; pass < 2; ++pass) {
         k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(A, I, K, rpb, c->qr_part, c->dflag);
         k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, Rinv, c->dflag);

@@ -24,7 +24,7 @@ def dtype_of(prec):
 class Ctx:
     """One library context built from host arrays copied to the device."""
 
-    def __init__(self, dims, idx, vals, U0, prec, chunk=0, qr_kind=0, host_inputs=False, stream=0):
+    def __init__(self, dims, idx, vals, U0, prec, chunk=0, qr_kind=0, host_inputs=False, stream=0, **opts):
         import torch
         self.torch = torch
         self.dims = tuple(int(d) for d in dims)
@@ -40,7 +40,7 @@ class Ctx:
             self._idx = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.int32)).cuda() for a in idx]
             self._vals = torch.from_numpy(np.ascontiguousarray(vals, dtype=npdt)).cuda()
             self._U0 = [torch.from_numpy(np.ascontiguousarray(u, dtype=npdt)).cuda() for u in U0]
-        opt = hoqri.hoqri_default_options(prec=prec, chunk_nnz=chunk, qr_kind=qr_kind)
+        opt = hoqri.hoqri_default_options(prec=prec, chunk_nnz=chunk, qr_kind=qr_kind, **opts)
         self.h = hoqri.hoqri_create(self.dims, self.ranks, len(vals), self._idx, self._vals, opt, self._U0, stream)
         self.dt = dt
 
