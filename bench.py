@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP32 comparison")
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="requests of the serving mix to stream through the server (0: skip)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -403,6 +405,12 @@ def run_ours(args):
            "final_resid": resid_last, "device_bytes": dev_bytes}
     if rank == 0 and world == 1 and not args.no_mixed and prec != hoqri.HOQRI_FP64:
         out["mixed_vs_fp32"] = mixed_vs_plain(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup)
+    if rank == 0 and world == 1 and args.serve_requests > 0:
+        from paper_2510_16930_gb300 import serve
+        out["serve"] = serve.serve_benchmark(n_req=args.serve_requests)
+        out["serve"]["workload"] = ("serving mix: Poisson arrivals at 0.8 x measured capacity, order 3 (p=0.7) "
+                                    "or 4, dims U[1e3,1e6], log10 nnz ~ N(5.5,0.5) in [4,7], Zipf(1.1), ranks "
+                                    "{4,8,16,32}, 10 sweeps each, FP32; a bounded sample of the 2000-request stream")
 
     # end to end through the public API from pinned host buffers
     if not args.no_e2e:

@@ -208,6 +208,61 @@ HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
 HOQRI_API hoqri_status hoqri_orthonormalize_noalloc(int32_t prec, int64_t I, int32_t K, const void *A_in,
                                                     void *U_out, void *stream);
 
+/* ---- Serving: many decompositions resident on one GPU (continuous batching).
+ * Not in the paper, which runs one decomposition at a time; the per-request
+ * arithmetic is exactly that of hoqri_create + hoqri_iterate (Alg. 2).
+ *
+ * A request is queued by hoqri_server_submit.  hoqri_server_step (called in
+ * the caller's loop, never blocks on the GPU) marks running requests whose
+ * sweeps have finished as done, then admits queued requests in submission
+ * order while the device-memory budget and the slot limit allow: an admitted
+ * request gets its own CUDA stream and context (sorted COO, factors, core
+ * resident on the device), and all of its sweeps are queued at once, each a
+ * replay of the context's captured sweep graph; requests on different streams
+ * overlap on the device.  A done request holds its memory until
+ * hoqri_server_take copies its results out and frees it.  Its results are
+ * those of the same request run alone (same kernels, same order).
+ * Ownership: the index and value buffers of a request (host or device) must
+ * stay valid until the request is admitted (state RUNNING or later).  Errors:
+ * the calls return a status; a request that fails at admission is reported
+ * FAILED by hoqri_server_poll / hoqri_server_take with its own status. */
+typedef struct hoqri_server hoqri_server;
+
+typedef struct {
+    int32_t N;                   /* order, 2..8 */
+    const int64_t *dims;         /* N mode sizes */
+    const int32_t *ranks;        /* N ranks (rules of hoqri_create) */
+    int64_t nnz;                 /* listed entries (repeats summed) */
+    const int32_t *const *idx;   /* N arrays of nnz 0-based indices (host or device) */
+    const void *vals;            /* nnz reals of the request's precision */
+    int32_t iters;               /* sweeps to run */
+    int32_t prec;                /* hoqri_precision */
+    uint64_t seed;               /* seeded Gaussian initial factors (orthonormalised) */
+} hoqri_request;
+
+enum { HOQRI_REQ_QUEUED = 0, HOQRI_REQ_RUNNING = 1, HOQRI_REQ_DONE = 2, HOQRI_REQ_FAILED = 3 };
+
+/* budget_bytes: device bytes the admitted requests may hold together (each is
+ * charged an estimate at admission, then its actual bytes); max_active: most
+ * requests running at once. */
+HOQRI_API hoqri_status hoqri_server_create(hoqri_server **out, int64_t budget_bytes, int32_t max_active);
+/* Queues a request; *id identifies it.  HOQRI_ERR_OOM if it alone exceeds the budget. */
+HOQRI_API hoqri_status hoqri_server_submit(hoqri_server *srv, const hoqri_request *req, int64_t *id);
+/* One scheduling round (see above); optional counts of running and queued requests. */
+HOQRI_API hoqri_status hoqri_server_step(hoqri_server *srv, int32_t *n_running, int32_t *n_queued);
+/* state (HOQRI_REQ_*), times[3] = submit, admission, completion (seconds on the
+ * server's steady clock; 0 if not reached), device bytes held (while QUEUED:
+ * the estimate admission will charge).  Each may be NULL. */
+HOQRI_API hoqri_status hoqri_server_poll(hoqri_server *srv, int64_t id, int32_t *state, double *times,
+                                         int64_t *device_bytes);
+/* Results of a DONE request into caller buffers (each may be NULL; host or
+ * device): U_out = N factor pointers, G_out = core, resid = fit after the last
+ * sweep.  Frees the request's device memory and forgets the id. */
+HOQRI_API hoqri_status hoqri_server_take(hoqri_server *srv, int64_t id, void *const *U_out, void *G_out,
+                                         double *resid);
+/* Frees every request and the server; NULL is a no-op. */
+HOQRI_API void hoqri_server_destroy(hoqri_server *srv);
+
 /* Message for the calling thread's last failed call ("" if none). */
 HOQRI_API const char *hoqri_last_error(void);
 

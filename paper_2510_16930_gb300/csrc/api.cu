@@ -16,9 +16,19 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string &msg) { g_last_error = msg; }
 
+cudaError_t raw_alloc(void **p, size_t bytes, cudaStream_t st) {
+    return st ? cudaMallocAsync(p, bytes, st) : cudaMalloc(p, bytes);
+}
+
+void raw_free(void *p, cudaStream_t st) {
+    if (!p) return;
+    if (st) cudaFreeAsync(p, st);
+    else cudaFree(p);
+}
+
 hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes) {
     *p = nullptr;
-    cudaError_t e = cudaMalloc(p, std::max<size_t>(bytes, 16));
+    cudaError_t e = raw_alloc(p, std::max<size_t>(bytes, 16), c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -29,9 +39,7 @@ hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes) {
     return HOQRI_OK;
 }
 
-void dfree(void *p) {
-    if (p) cudaFree(p);
-}
+void dfree(void *p, cudaStream_t st) { raw_free(p, st); }
 
 static bool is_device_ptr(const void *p) {
     if (!p) return false;
@@ -64,7 +72,7 @@ static hoqri_status ensure_slots(hoqri_ctx *c, int64_t slots) {
     if (c->dnorm) {
         HQ_CUDA(cudaMemcpyAsync(nd, c->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
         HQ_CUDA(cudaStreamSynchronize(c->stream));
-        dfree(c->dnorm);
+        dfree(c->dnorm, c->stream);
     }
     c->dnorm = nd;
     c->dnorm_slots = slots;
@@ -78,6 +86,7 @@ static hoqri_status ensure_slots(hoqri_ctx *c, int64_t slots) {
 static void destroy_impl(hoqri_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaStream_t st = c->stream;
     if (c->sweep_exec) cudaGraphExecDestroy(c->sweep_exec);
     for (auto &r : c->ev_recs) {
         cudaEventDestroy(r.a);
@@ -86,41 +95,41 @@ static void destroy_impl(hoqri_ctx *c) {
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     for (int n = 0; n < HOQRI_MAXN; ++n) {
         ModeStore &M = c->ms[n];
-        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.oidx[j]);
-        dfree(M.vals);
-        dfree(M.perm);
-        dfree(M.row_id);
-        dfree(M.row_ptr);
-        dfree(M.chunk_start);
-        dfree(M.chunk_row);
-        dfree(M.big);
-        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.hidx[j]);
-        dfree(M.hvals);
-        dfree(M.lrp);
-        dfree(M.lrow);
-        dfree(M.sbase);
-        dfree(M.srow);
-        dfree(M.item_s);
-        dfree(M.item_e);
-        dfree(M.item_aux);
-        dfree(M.span);
-        dfree(c->U[n]);
+        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.oidx[j], st);
+        dfree(M.vals, st);
+        dfree(M.perm, st);
+        dfree(M.row_id, st);
+        dfree(M.row_ptr, st);
+        dfree(M.chunk_start, st);
+        dfree(M.chunk_row, st);
+        dfree(M.big, st);
+        for (int j = 0; j < HOQRI_MAXN - 1; ++j) dfree(M.hidx[j], st);
+        dfree(M.hvals, st);
+        dfree(M.lrp, st);
+        dfree(M.lrow, st);
+        dfree(M.sbase, st);
+        dfree(M.srow, st);
+        dfree(M.item_s, st);
+        dfree(M.item_e, st);
+        dfree(M.item_aux, st);
+        dfree(M.span, st);
+        dfree(c->U[n], st);
     }
-    dfree(c->gslot);
-    dfree(c->gcount);
-    dfree(c->G);
-    dfree(c->A);
-    dfree(c->dnorm);
-    dfree(c->dflag);
-    dfree(c->core_part);
-    dfree(c->a_part);
-    dfree(c->qr_part);
-    dfree(c->qr_small);
-    dfree(c->qr_work);
-    dfree(c->gnorm_part);
-    dfree(c->Y);
-    dfree(c->ypart);
-    dfree(c->usplit);
+    dfree(c->gslot, st);
+    dfree(c->gcount, st);
+    dfree(c->G, st);
+    dfree(c->A, st);
+    dfree(c->dnorm, st);
+    dfree(c->dflag, st);
+    dfree(c->core_part, st);
+    dfree(c->a_part, st);
+    dfree(c->qr_part, st);
+    dfree(c->qr_small, st);
+    dfree(c->qr_work, st);
+    dfree(c->gnorm_part, st);
+    dfree(c->Y, st);
+    dfree(c->ypart, st);
+    dfree(c->usplit, st);
     cudaGetLastError();
     delete c;
 }
@@ -338,7 +347,7 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
     // inputs on the device (temporaries released after set-up)
     std::vector<void *> tmp;
     auto free_tmp = [&]() {
-        for (void *p : tmp) cudaFree(p);
+        for (void *p : tmp) raw_free(p, c->stream);
         tmp.clear();
     };
     const int32_t *idx_dev[HOQRI_MAXN] = {};
@@ -348,7 +357,7 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
             idx_dev[n] = idx[n];
         } else {
             void *p = nullptr;
-            if (cudaMalloc(&p, nnz * sizeof(int32_t)) != cudaSuccess) {
+            if (raw_alloc(&p, nnz * sizeof(int32_t), c->stream) != cudaSuccess) {
                 cudaGetLastError();
                 free_tmp();
                 set_error("hoqri_create: device allocation for the indices failed");
@@ -365,7 +374,7 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
     }
     if (nnz > 0 && !is_device_ptr(vals)) {
         void *p = nullptr;
-        if (cudaMalloc(&p, nnz * c->rsize) != cudaSuccess) {
+        if (raw_alloc(&p, nnz * c->rsize, c->stream) != cudaSuccess) {
             cudaGetLastError();
             free_tmp();
             set_error("hoqri_create: device allocation for the values failed");
@@ -458,7 +467,7 @@ hoqri_status hoqri_orthonormalize(hoqri_ctx *c, int32_t mode, const void *A_in, 
         hoqri_status s = orthonormalize(c, mode, c->A, tmp);
         if (s == HOQRI_OK) s = copy_out(c, U_out, tmp, bytes);
         cudaStreamSynchronize(c->stream);
-        dfree(tmp);
+        dfree(tmp, c->stream);
         c->device_bytes -= (int64_t)std::max<size_t>(bytes, 16);
         if (s != HOQRI_OK) return s;
     }

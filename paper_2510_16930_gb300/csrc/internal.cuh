@@ -159,8 +159,14 @@ struct hoqri_ctx {
 namespace hoqri {
 
 // device memory helpers (track bytes)
+// Device memory of a context.  A context on a created stream allocates and
+// frees in stream order (cudaMallocAsync / cudaFreeAsync), so creating and
+// destroying contexts does not wait for work on other streams; on the legacy
+// default stream plain cudaMalloc / cudaFree are used.
+cudaError_t raw_alloc(void **p, size_t bytes, cudaStream_t st);
+void raw_free(void *p, cudaStream_t st);
 hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes);
-void dfree(void *p);
+void dfree(void *p, cudaStream_t st = nullptr);
 
 // setup (setup.cu)
 hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw);

@@ -170,14 +170,16 @@ __global__ void k_hyb_gather(IdxPack src, IdxPackW dst, int nm1, const int32_t *
 
 // RAII holder for set-up temporaries
 struct Tmp {
+    cudaStream_t st;
     std::vector<void *> ptrs;
+    explicit Tmp(cudaStream_t s) : st(s) {}
     ~Tmp() {
-        for (void *p : ptrs) cudaFree(p);
+        for (void *p : ptrs) raw_free(p, st);
     }
     template <typename T>
     hoqri_status get(T **p, size_t count) {
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+        cudaError_t e = raw_alloc(&q, std::max<size_t>(count, 1) * sizeof(T), st);
         if (e != cudaSuccess) {
             set_error(std::string("set-up allocation: ") + cudaGetErrorString(e));
             return HOQRI_ERR_OOM;
@@ -200,7 +202,7 @@ template <typename T>
 static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw) {
     cudaStream_t st = c->stream;
     const int N = c->N;
-    Tmp tmp;
+    Tmp tmp(c->stream);
     const int G = std::min(grid_for(nnz_raw), c->num_sms * 8);
     IdxPack in{};
     for (int m = 0; m < N; ++m) in.p[m] = idx_dev[m];
@@ -373,9 +375,9 @@ hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const vo
 hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C) {
     ModeStore &M = c->ms[n];
     cudaStream_t st = c->stream;
-    dfree(M.chunk_start);
-    dfree(M.chunk_row);
-    dfree(M.big);
+    dfree(M.chunk_start, c->stream);
+    dfree(M.chunk_row, c->stream);
+    dfree(M.big, c->stream);
     M.chunk_start = nullptr;
     M.chunk_row = nullptr;
     M.big = nullptr;
@@ -525,7 +527,7 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     M.nitem_long = nitem_long;
     M.nitem = (int64_t)is.size();
     M.nspan = (int64_t)span.size() / 3;
-    Tmp tmp;
+    Tmp tmp(c->stream);
     int32_t *dmap;
     HQ_TRY(tmp.get(&dmap, total + 16));
     HQ_CUDA(cudaMemcpyAsync(dmap, map.data(), (total + 16) * sizeof(int32_t), cudaMemcpyHostToDevice, st));

@@ -25,12 +25,20 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
            "hoqri_iterate", "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
            "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
-           "hoqri_destroy", "hoqri_orthonormalize_noalloc")
+           "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
+           "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take", "hoqri_server_destroy")
+HOQRI_REQ_QUEUED, HOQRI_REQ_RUNNING, HOQRI_REQ_DONE, HOQRI_REQ_FAILED = range(4)
 
 
 class hoqri_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("qr_kind", C.c_int32), ("chunk_nnz", C.c_int32), ("autotune", C.c_int32),
                 ("use_graphs", C.c_int32), ("one_stream", C.c_int32), ("seed", C.c_uint64), ("tol", C.c_double)]
+
+
+class hoqri_request(C.Structure):
+    _fields_ = [("N", C.c_int32), ("dims", C.POINTER(C.c_int64)), ("ranks", C.POINTER(C.c_int32)),
+                ("nnz", C.c_int64), ("idx", C.POINTER(C.c_void_p)), ("vals", C.c_void_p), ("iters", C.c_int32),
+                ("prec", C.c_int32), ("seed", C.c_uint64)]
 
 
 class HoqriError(RuntimeError):
@@ -74,11 +82,19 @@ def load(build_if_missing: bool = True):
     L.hoqri_synchronize.argtypes = [vp]
     L.hoqri_last_error.restype = C.c_char_p
     L.hoqri_orthonormalize_noalloc.argtypes = [i32, i64, i32, vp, vp, vp]
+    L.hoqri_server_create.argtypes = [C.POINTER(vp), i64, i32]
+    L.hoqri_server_submit.argtypes = [vp, C.POINTER(hoqri_request), C.POINTER(i64)]
+    L.hoqri_server_step.argtypes = [vp, C.POINTER(i32), C.POINTER(i32)]
+    L.hoqri_server_poll.argtypes = [vp, i64, C.POINTER(i32), C.POINTER(C.c_double), C.POINTER(i64)]
+    L.hoqri_server_take.argtypes = [vp, i64, C.POINTER(vp), vp, C.POINTER(C.c_double)]
+    L.hoqri_server_destroy.argtypes = [vp]
+    L.hoqri_server_destroy.restype = None
     L.hoqri_destroy.argtypes = [vp]
     L.hoqri_destroy.restype = None
     for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate",
                  "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_synchronize",
-                 "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc"):
+                 "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
+                 "hoqri_server_submit", "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -198,3 +214,54 @@ def hoqri_last_error() -> str:
 def hoqri_destroy(ctx):
     if ctx:
         load().hoqri_destroy(ctx)
+
+
+# ---- serving
+
+def hoqri_server_create(budget_bytes, max_active):
+    h = C.c_void_p()
+    _check(load().hoqri_server_create(C.byref(h), int(budget_bytes), int(max_active)))
+    return h.value
+
+
+def hoqri_server_submit(srv, dims, ranks, nnz, idx, vals, iters, prec, seed=0):
+    """Queues a request; idx / vals (host or device) must stay alive until it is
+    admitted.  Returns the request id."""
+    N = len(dims)
+    keep = ((C.c_int64 * N)(*[int(v) for v in dims]), (C.c_int32 * N)(*[int(v) for v in ranks]),
+            (C.c_void_p * N)(*[_addr(a) for a in idx]))
+    q = hoqri_request(N, keep[0], keep[1], int(nnz), keep[2], _addr(vals), int(iters), int(prec), int(seed))
+    rid = C.c_int64()
+    _check(load().hoqri_server_submit(srv, C.byref(q), C.byref(rid)))
+    return rid.value
+
+
+def hoqri_server_step(srv):
+    """One scheduling round; returns (running, queued)."""
+    r, q = C.c_int32(), C.c_int32()
+    _check(load().hoqri_server_step(srv, C.byref(r), C.byref(q)))
+    return r.value, q.value
+
+
+def hoqri_server_poll(srv, rid):
+    """(state, (t_submit, t_admit, t_done), device_bytes); raises for a failed request."""
+    st, b = C.c_int32(), C.c_int64()
+    t = (C.c_double * 3)()
+    _check(load().hoqri_server_poll(srv, int(rid), C.byref(st), t, C.byref(b)))
+    return st.value, tuple(t), b.value
+
+
+def hoqri_server_take(srv, rid, U_out=None, G_out=None):
+    """Copies the results of a finished request out (buffers may be None) and
+    frees it; returns the residual of the last sweep."""
+    ua = None
+    if U_out is not None:
+        ua = (C.c_void_p * len(U_out))(*[_addr(u) for u in U_out])
+    r = C.c_double()
+    _check(load().hoqri_server_take(srv, int(rid), ua, _addr(G_out), C.byref(r)))
+    return r.value
+
+
+def hoqri_server_destroy(srv):
+    if srv:
+        load().hoqri_server_destroy(srv)

@@ -223,10 +223,11 @@ class ServeRequest:
 
 def serving_mix(n_req: int, rate_hz: float, seed: int, dim_range=(1_000, 1_000_000),
                 log_nnz=(5.5, 0.5, 4.0, 7.0), rank_set=(4, 8, 16, 32),
-                p_order3: float = 0.7) -> list:
+                p_order3: float = 0.7, max_pm: int = 2048) -> list:
     """Poisson arrivals of decomposition requests (order 3 w.p. p_order3 else 4).
 
-    Ranks are redrawn per request until K_n <= I_n and K_n <= prod_{m!=n} K_m."""
+    Ranks are redrawn per request until K_n <= I_n, K_n <= prod_{m!=n} K_m and
+    prod_{m!=n} K_m <= max_pm (the largest Kronecker row the passes support)."""
     r = _rng(seed, _P_MIX)
     ra = _rng(seed, _P_ARR)
     t = 0.0
@@ -239,7 +240,7 @@ def serving_mix(n_req: int, rate_hz: float, seed: int, dim_range=(1_000, 1_000_0
         nnz = int(round(10 ** float(np.clip(r.normal(mu, sd), lo, hi))))
         while True:
             ranks = tuple(int(v) for v in r.choice(rank_set, size=N))
-            if all(ranks[n] <= dims[n] and ranks[n] <= math.prod(ranks[:n] + ranks[n + 1:])
+            if all(ranks[n] <= dims[n] and ranks[n] <= math.prod(ranks[:n] + ranks[n + 1:]) <= max_pm
                    for n in range(N)):
                 break
         out.append(ServeRequest(q, t, dims, ranks, nnz, (seed * 1000003 + q) & 0x7FFFFFFF))

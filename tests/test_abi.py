@@ -62,3 +62,26 @@ def test_noalloc_rejects_bad_arguments_before_device_work():
         with pytest.raises(hoqri.HoqriError) as e:
             hoqri.hoqri_orthonormalize_noalloc(prec, I, K, 0, 0)
         assert e.value.code == hoqri.HOQRI_ERR_INVALID and frag in str(e.value)
+
+
+def test_server_rejects_bad_requests_without_gpu_work():
+    """Server creation and submission validate on the host; nothing runs until a step."""
+    import numpy as np
+    import pytest
+    srv = hoqri.hoqri_server_create(1 << 30, 4)
+    try:
+        idx = [np.zeros(10, np.int32)] * 3
+        vals = np.ones(10, np.float32)
+        with pytest.raises(hoqri.HoqriError) as e:
+            hoqri.hoqri_server_submit(srv, (10,), (2,), 10, idx[:1], vals, 1, hoqri.HOQRI_FP32)
+        assert e.value.code == hoqri.HOQRI_ERR_INVALID
+        with pytest.raises(hoqri.HoqriError) as e:  # alone larger than the budget
+            hoqri.hoqri_server_submit(srv, (10**6,) * 3, (32,) * 3, 10**9, idx, vals, 1, hoqri.HOQRI_FP32)
+        assert e.value.code == hoqri.HOQRI_ERR_OOM
+        rid = hoqri.hoqri_server_submit(srv, (10, 10, 10), (2, 2, 2), 10, idx, vals, 1, hoqri.HOQRI_FP32)
+        st, t, b = hoqri.hoqri_server_poll(srv, rid)
+        assert st == hoqri.HOQRI_REQ_QUEUED and b == 0
+    finally:
+        hoqri.hoqri_server_destroy(srv)
+    with pytest.raises(hoqri.HoqriError):
+        hoqri.hoqri_server_create(0, 4)
