@@ -75,7 +75,10 @@ typedef struct {
                            down; 1: Householder only; 2: CholeskyQR2, breakdown is an
                            error (HOQRI_ERR_QR_BREAKDOWN) */
     int32_t chunk_nnz;  /* nonzeros per warp task; 0 = chosen by the library */
-    int32_t autotune;   /* 1: time the candidate chunk sizes once at create */
+    int32_t autotune;   /* 1: at create, time candidate layouts of the nonzero-stream
+                           pass per mode (long-row threshold, work-item size) and keep
+                           the fastest; cached per problem kind, and in the file named by
+                           the environment variable HOQRI_TUNE_CACHE if set */
     int32_t use_graphs; /* 1: hoqri_iterate replays one sweep as a CUDA graph */
     int32_t one_stream; /* 0/1: FP32 modes with a register-tile plan stream their nonzeros
                            once per block update and keep Y_(n) (R_n x P_{-n} floats) for

@@ -417,6 +417,7 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
     } else {
         if ((s = init_factors_seeded(c)) != HOQRI_OK) return fail(s);
     }
+    if (c->opt.autotune && (s = autotune_hybrid(c)) != HOQRI_OK) return fail(s);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
         set_error("hoqri_create: CUDA error during set-up");
         return fail(HOQRI_ERR_CUDA);

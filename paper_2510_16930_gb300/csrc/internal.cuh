@@ -87,6 +87,9 @@ struct ModeStore {
     int64_t ipw = 1, nrange = 0;         // warp w processes items [w*ipw, (w+1)*ipw)
     int64_t nspan = 0;
     int32_t *span = nullptr;             // [3*nspan] (long row j, first range, last range) of rows cut by ranges
+    int64_t tune_Lshort = 0, tune_T = 0; // the layout parameters it was built with
+    int64_t long_elems = 0;              // nonzeros in the long part
+    int64_t hyb_bytes = 0;               // device bytes of the hybrid arrays
 };
 
 struct Workspace;  // defined in the pass unit
@@ -172,6 +175,8 @@ void dfree(void *p, cudaStream_t st = nullptr);
 hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw);
 hoqri_status build_partition(hoqri_ctx *c, int n, int32_t C);
 hoqri_status build_hybrid(hoqri_ctx *c, int n, int64_t Lshort, int64_t T, int SW);
+void free_hybrid(hoqri_ctx *c, int n);             // releases what build_hybrid allocated
+hoqri_status autotune_hybrid(hoqri_ctx *c);        // tune.cu: layout per mode by timing
 
 // register-tile plan of the FP32 kernels for mode n (passes.cu)
 struct FastTile {

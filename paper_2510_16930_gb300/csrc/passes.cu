@@ -972,7 +972,9 @@ hoqri_status passes_init(hoqri_ctx *c) {
         const ModeStore &M = c->ms[n];
         ab = std::max<int64_t>(ab, std::max<int64_t>(M.nitem_long, 1) * 2 * c->K[n] * (int64_t)c->rsize);
         ybytes = std::max<int64_t>(ybytes, M.R * (int64_t)p.Pm * 4);
-        ypb = std::max<int64_t>(ypb, std::max<int64_t>(M.nrange, 1) * 2 * (int64_t)p.Pm * 4);
+        // pieces of rows cut by warp ranges: at most one range per warp of the pass
+        // (any layout the autotuner may build)
+        ypb = std::max<int64_t>(ypb, (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8 * 2 * (int64_t)p.Pm * 4);
     }
     c->a_part_bytes = ab;
     HQ_TRY(dalloc(c, &c->a_part, c->a_part_bytes));

@@ -452,6 +452,7 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     std::vector<int64_t> lrp(nlong + 1, 0);
     for (int64_t j = 0; j < nlong; ++j) lrp[j + 1] = lrp[j] + (rp[lrow[j] + 1] - rp[lrow[j]]);
     const int64_t total_long = lrp[nlong];
+    M.long_elems = total_long;
     const int64_t nslice = ((int64_t)srt.size() + SW - 1) / SW;
     std::vector<int64_t> sbase(nslice + 1);
     std::vector<int32_t> srow((size_t)SW * nslice, -1);
@@ -562,8 +563,33 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
 
 hoqri_status build_hybrid(hoqri_ctx *c, int n, int64_t Lshort, int64_t T, int SW) {
     const int64_t T32 = std::max<int64_t>(32, (T + 31) & ~(int64_t)31);
-    if (c->prec == HOQRI_FP64) return build_hybrid_t<double>(c, n, Lshort, T32, SW);
-    return build_hybrid_t<float>(c, n, Lshort, T32, SW);
+    const int64_t b0 = c->device_bytes;
+    hoqri_status s = c->prec == HOQRI_FP64 ? build_hybrid_t<double>(c, n, Lshort, T32, SW)
+                                            : build_hybrid_t<float>(c, n, Lshort, T32, SW);
+    ModeStore &M = c->ms[n];
+    M.tune_Lshort = Lshort;
+    M.tune_T = T;
+    M.hyb_bytes = c->device_bytes - b0;
+    return s;
+}
+
+void free_hybrid(hoqri_ctx *c, int n) {
+    ModeStore &M = c->ms[n];
+    cudaStream_t st = c->stream;
+    for (int j = 0; j < HOQRI_MAXN - 1; ++j) {
+        dfree(M.hidx[j], st);
+        M.hidx[j] = nullptr;
+    }
+    void **arrs[] = {&M.hvals, (void **)&M.lrp, (void **)&M.lrow, (void **)&M.sbase, (void **)&M.srow,
+                     (void **)&M.item_s, (void **)&M.item_e, (void **)&M.item_aux, (void **)&M.span};
+    for (void **a : arrs) {
+        dfree(*a, st);
+        *a = nullptr;
+    }
+    c->device_bytes -= M.hyb_bytes;
+    M.hyb_bytes = 0;
+    M.hyb = false;
+    M.nitem = M.nitem_long = M.nlong = M.nslice = M.nspan = M.htotal = 0;
 }
 
 }  // namespace hoqri

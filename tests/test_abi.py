@@ -80,7 +80,7 @@ def test_server_rejects_bad_requests_without_gpu_work():
         assert e.value.code == hoqri.HOQRI_ERR_OOM
         rid = hoqri.hoqri_server_submit(srv, (10, 10, 10), (2, 2, 2), 10, idx, vals, 1, hoqri.HOQRI_FP32)
         st, t, b = hoqri.hoqri_server_poll(srv, rid)
-        assert st == hoqri.HOQRI_REQ_QUEUED and b == 0
+        assert st == hoqri.HOQRI_REQ_QUEUED and b > 0  # while queued: the admission estimate
     finally:
         hoqri.hoqri_server_destroy(srv)
     with pytest.raises(hoqri.HoqriError):
