@@ -58,6 +58,19 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def replica_throughput(ms, units, world, device="cpu"):
+    """Replicas (one independent workload per rank): the job's time is the slowest
+    rank's, value = units processed by all ranks / that time.  Returns (value, max ms)."""
+    ms_max = float(ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_max], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    return units * world / (ms_max / 1e3), ms_max
+
+
 # ----------------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -379,12 +392,7 @@ def run_ours(args):
     hoqri.hoqri_iterate(ctx, min(args.steps, 5), want_hist=False)
     prof, _ = hoqri.hoqri_profile_read(ctx)
     hoqri.hoqri_profile_enable(ctx, False)
-    ms_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = nnz_c * N * args.steps * world / (ms_max / 1e3)
+    value, ms_max = replica_throughput(ms, nnz_c * N * args.steps, world, "cuda")
 
     # roofline of the dominant kernel: the pass over a mode's nonzero stream
     # (k_hyb, long-row and slice launches), timed by its own CUDA events
