@@ -566,10 +566,14 @@ __global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nbl
     }
 }
 
+// out = sum of part[0..n) by one warp: lane-strided sums, then a fixed butterfly
 __global__ void k_sum_into(const double *part, int n, double *out, double *out2) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < n; ++i) s += part[i];
+    const int lane = threadIdx.x & 31;
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    double s = 0.0;
+    for (int i = lane; i < n; i += 32) s += part[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
         *out = s;
         if (out2) *out2 = s;
     }

@@ -76,78 +76,97 @@ __global__ void __launch_bounds__(GRAM_TPB) k_gram_partial(const T *A, int64_t I
     }
 }
 
+// 1 / sqrt(d) in FP64 for 1e-30 < d < 1e30: the FP32 estimate refined by two
+// Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which doubles the number
+// of correct bits (about 22 -> 44 -> full FP64).  FP64 divisions and square
+// roots are long instruction sequences on this GPU; a pivot of the Cholesky
+// needs both, and the pivots are sequential.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    y = y * (1.5 - 0.5 * d * y * y);
+    y = y * (1.5 - 0.5 * d * y * y);
+    return y;
+}
+
 // Sum of the Gram partials in block order, Cholesky W = R^T R, Rinv = R^{-1}.
-// R overwrites the upper triangle of W in place (row j of R is formed from row
-// j of W and the rows of R above it).
+// The partial sums use all warps; the factorisation and the inverse run in
+// warp 0 (lane k holds column k), so the sequential pivots need no block
+// barrier.  R overwrites the upper triangle of W in place.
 __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int K, double *Rinv, int32_t *flag) {
     if (*flag != 0) return;
     __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
-    __shared__ int broke;
+    __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j)
     const int npairs = K * (K + 1) / 2;
-    // W(i, j) = sum of the block partials: one warp per pair, lanes stride the
-    // blocks, then a fixed butterfly (same order every run)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int p = wid; p < npairs; p += nwarp) {
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * npairs + p];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            int rem = p, i = 0;
-            while (rem >= K - i) {
-                rem -= K - i;
-                ++i;
-            }
-            W[i * K + i + rem] = s;
+    // W(i, j) = sum of the block partials: thread per pair (coalesced across the
+    // threads for each block), eight interleaved partial sums so eight loads are
+    // in flight, combined in a fixed order (same result every run)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+        double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int b = 0;
+        for (; b + 8 <= nblk; b += 8)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s8[u] += part[(size_t)(b + u) * npairs + p];
+        for (int u = 0; b < nblk; ++b, ++u) s8[u] += part[(size_t)b * npairs + p];
+        const double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+        int rem = p, i = 0;
+        while (rem >= K - i) {
+            rem -= K - i;
+            ++i;
         }
+        W[i * K + i + rem] = s;
     }
-    __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j): one division per pivot
-    if (threadIdx.x == 0) broke = 0;
     __syncthreads();
+    if (wid != 0) return;
     double dmax = 0.0;
     for (int i = 0; i < K; ++i) dmax = fmax(dmax, W[i * K + i]);
     const double tiny = 1e-14 * dmax;
-    for (int j = 0; j < K; ++j) {
-        if (threadIdx.x == 0) {
-            double d = W[j * K + j];
-            for (int i = 0; i < j; ++i) d -= W[i * K + j] * W[i * K + j];
-            if (!(d > tiny) || !(dmax > 0.0)) broke = 1;
-            const double r = broke ? 1.0 : sqrt(d);
-            W[j * K + j] = r;
-            inv[j] = 1.0 / r;
-        }
-        __syncthreads();
-        const double ij = inv[j];
-        for (int k = j + 1 + threadIdx.x; k < K; k += blockDim.x) {
+    int bad = !(dmax > 0.0);
+    for (int j = 0; j < K && !bad; ++j) {
+        // pivot: d = W(j,j) - sum_{i<j} R(i,j)^2, a lane-strided sum in fixed order
+        double d = 0.0;
+        for (int i = lane; i < j; i += 32) d += W[i * K + j] * W[i * K + j];
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        d = W[j * K + j] - d;
+        bad = !(d > tiny);
+        if (bad) break;
+        const double y = rsqrt_fp64(d);  // 1 / R(j, j)
+        // row j of R: R(j,k) = (W(j,k) - sum_{i<j} R(i,j) R(i,k)) / R(j,j), lane per k
+        for (int k = j + 1 + lane; k < K; k += 32) {
             double s = W[j * K + k];
             for (int i = 0; i < j; ++i) s -= W[i * K + j] * W[i * K + k];
-            W[j * K + k] = s * ij;
+            W[j * K + k] = s * y;
         }
-        __syncthreads();
+        __syncwarp();
+        if (lane == 0) {
+            W[j * K + j] = d * y;
+            inv[j] = y;
+        }
+        __syncwarp();
     }
-    if (broke) {
-        if (threadIdx.x == 0) {
+    if (bad) {
+        if (lane == 0) {
             *flag = 1;
             flag[1] += 1;
         }
         return;
     }
-    // Rinv: solve R X = I column by column (X upper triangular).  R occupies the
-    // upper triangle of W; X(i, col) for i < col goes to the free strictly-lower
-    // entry W(col, i), the diagonal to Xd, so no second K x K array is needed.
-    __shared__ double Xd[HOQRI_MAXK];
-    for (int col = threadIdx.x; col < K; col += blockDim.x) {
-        for (int i = col; i >= 0; --i) {
-            double s = (i == col) ? 1.0 : 0.0;
-            for (int k = i + 1; k <= col; ++k) s -= W[i * K + k] * (k == col ? Xd[col] : W[col * K + k]);
-            const double v = s * inv[i];
-            if (i == col) Xd[col] = v;
-            else W[col * K + i] = v;
+    // Rinv: lane col solves R x = e_col by back substitution (x upper triangular);
+    // x(i) for i < col is kept in the free strictly-lower entry W(col, i)
+    for (int col = lane; col < K; col += 32) {
+        const double xd = inv[col];
+        for (int i = col - 1; i >= 0; --i) {
+            double s = -W[i * K + col] * xd;
+            for (int k = i + 1; k < col; ++k) s -= W[i * K + k] * W[col * K + k];
+            W[col * K + i] = s * inv[i];
         }
+        Rinv[col * K + col] = xd;
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+    __syncwarp();
+    for (int t = lane; t < K * K; t += 32) {
         const int i = t / K, col = t - i * K;
-        Rinv[t] = i > col ? 0.0 : (i == col ? Xd[col] : W[col * K + i]);
+        if (i != col) Rinv[t] = i > col ? 0.0 : W[col * K + i];
     }
 }
 
@@ -163,8 +182,20 @@ __global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
         T a[KC], o[KC];
+        if constexpr (sizeof(T) == 4 && KC % 4 == 0) {
+            // a row is KC/4 aligned 16-byte vectors
 #pragma unroll
-        for (int i = 0; i < KC; ++i) a[i] = A[r * KC + i];
+            for (int i = 0; i < KC / 4; ++i) {
+                const float4 v = reinterpret_cast<const float4 *>(A + r * KC)[i];
+                a[4 * i] = v.x;
+                a[4 * i + 1] = v.y;
+                a[4 * i + 2] = v.z;
+                a[4 * i + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < KC; ++i) a[i] = A[r * KC + i];
+        }
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
             T s = T(0);
@@ -172,8 +203,15 @@ __global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const
             for (int i = 0; i <= c; ++i) s = fma(a[i], Rs[i * KC + c], s);
             o[c] = s;
         }
+        if constexpr (sizeof(T) == 4 && KC % 4 == 0) {
 #pragma unroll
-        for (int c = 0; c < KC; ++c) out[r * KC + c] = o[c];
+            for (int i = 0; i < KC / 4; ++i)
+                reinterpret_cast<float4 *>(out + r * KC)[i] =
+                    make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < KC; ++c) out[r * KC + c] = o[c];
+        }
     }
 }
 
@@ -199,6 +237,12 @@ __global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, i
 template <typename T>
 void launch_apply(cudaStream_t st, const int32_t *flag, const T *A, int64_t I, int K, const double *Rinv, T *out,
                   int grid) {
+    // the fixed-width kernels move FP32 rows as 16-byte vectors: both buffers must be 16-byte aligned
+    const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
+    if (!aligned) {
+        k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag);
+        return;
+    }
     switch (K) {
         case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
         case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;

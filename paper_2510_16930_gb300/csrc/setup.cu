@@ -486,15 +486,18 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
         }
     }
     const int64_t nitem_long = (int64_t)is.size();
-    // slice items of about T8 cost units: one per stored element plus P_{-n}/8
-    // per row (the row of Y it writes), so items of many tiny rows stay small
+    // slice items of about T8/8 cost units: one per stored element plus P_{-n}/8
+    // per row (the row of Y it writes), so items of many tiny rows stay small.
+    // Slice items are dealt round-robin to the warps; at an eighth of the long
+    // item size each warp gets some twenty, which keeps the SMs level.
     int64_t Pm = 1;
     for (int m = 0; m < c->N; ++m)
         if (m != n) Pm *= c->K[m];
     const int64_t row_cost = std::max<int64_t>(1, Pm / 8);
+    const int64_t Ts = std::max<int64_t>(256, T8 / 8);
     for (int64_t j = 0; j < nslice;) {
         int64_t k = j, cost = 0;
-        while (k < nslice && cost < T8) {
+        while (k < nslice && cost < Ts) {
             cost += (sbase[k + 1] - sbase[k]) + (int64_t)SW * row_cost;
             ++k;
         }
