@@ -168,6 +168,30 @@ __global__ void k_hyb_gather(IdxPack src, IdxPackW dst, int nm1, const int32_t *
     }
 }
 
+// map of the long part: position lrp[j] + q holds sorted position row_ptr[lrow[j]] + q
+__global__ void k_map_long(const int64_t *lrp, const int32_t *lrow, const int64_t *row_ptr, int64_t nlong,
+                           int32_t *map) {
+    for (int64_t j = blockIdx.x; j < nlong; j += gridDim.x) {
+        const int64_t a = lrp[j], len = lrp[j + 1] - a, s = row_ptr[lrow[j]];
+        for (int64_t q = threadIdx.x; q < len; q += blockDim.x) map[a + q] = (int32_t)(s + q);
+    }
+}
+
+// map of the slices: position sbase[j] + SW*q + g holds sorted position
+// row_ptr[r] + q of the slice's row g (r = srow[SW*j + g]) for q < its length
+__global__ void k_map_slices(const int64_t *sbase, const int32_t *srow, const int64_t *row_ptr, int64_t nslice, int SW,
+                             int32_t *map) {
+    for (int64_t j = blockIdx.x; j < nslice; j += gridDim.x) {
+        const int64_t b = sbase[j], e = sbase[j + 1];
+        for (int64_t p = b + threadIdx.x; p < e; p += blockDim.x) {
+            const int64_t off = p - b, q = off / SW;
+            const int g = (int)(off - q * SW);
+            const int32_t r = srow[SW * j + g];
+            if (r >= 0 && q < row_ptr[r + 1] - row_ptr[r]) map[p] = (int32_t)(row_ptr[r] + q);
+        }
+    }
+}
+
 // RAII holder for set-up temporaries
 struct Tmp {
     cudaStream_t st;
@@ -464,15 +488,6 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
         sbase[j + 1] = sbase[j] + ((SW * L + 3) & ~(int64_t)3);
     }
     const int64_t total = sbase[nslice];
-    std::vector<int32_t> map(total + 16, -1);
-    for (int64_t j = 0; j < nlong; ++j)
-        for (int64_t q = 0; q < lrp[j + 1] - lrp[j]; ++q) map[lrp[j] + q] = (int32_t)(rp[lrow[j]] + q);
-    for (int64_t j = 0; j < nslice; ++j)
-        for (int g = 0; g < SW; ++g) {
-            const int32_t r = srow[SW * j + g];
-            if (r < 0) continue;
-            for (int64_t q = 0; q < rp[r + 1] - rp[r]; ++q) map[sbase[j] + SW * q + g] = (int32_t)(rp[r] + q);
-        }
     // work items: long tasks of T8 elements, then runs of slices of about T8 elements
     std::vector<int64_t> is, ie;
     std::vector<int32_t> ia, span;
@@ -531,20 +546,6 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     M.nitem_long = nitem_long;
     M.nitem = (int64_t)is.size();
     M.nspan = (int64_t)span.size() / 3;
-    Tmp tmp(c->stream);
-    int32_t *dmap;
-    HQ_TRY(tmp.get(&dmap, total + 16));
-    HQ_CUDA(cudaMemcpyAsync(dmap, map.data(), (total + 16) * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    IdxPack src{};
-    IdxPackW dst{};
-    for (int j = 0; j < nm1; ++j) {
-        HQ_TRY(dalloc(c, (void **)&M.hidx[j], (total + 16) * sizeof(int32_t)));
-        src.p[j] = M.oidx[j];
-        dst.p[j] = M.hidx[j];
-    }
-    HQ_TRY(dalloc(c, &M.hvals, (total + 16) * sizeof(T)));
-    k_hyb_gather<T><<<std::min(grid_for(total + 16), c->num_sms * 8), TPB, 0, st>>>(
-        src, dst, nm1, dmap, total + 16, (const T *)M.vals, (T *)M.hvals);
     auto up = [&](auto **d, const auto &v) -> hoqri_status {
         using E = typename std::decay<decltype(v[0])>::type;
         HQ_TRY(dalloc(c, (void **)d, std::max<size_t>(v.size(), 1) * sizeof(E)));
@@ -555,6 +556,26 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     HQ_TRY(up(&M.lrow, lrow));
     HQ_TRY(up(&M.sbase, sbase));
     HQ_TRY(up(&M.srow, srow));
+    // hybrid position -> sorted position (-1: padding), built on the device
+    Tmp tmp(c->stream);
+    int32_t *dmap;
+    HQ_TRY(tmp.get(&dmap, total + 16));
+    HQ_CUDA(cudaMemsetAsync(dmap, 0xFF, (total + 16) * sizeof(int32_t), st));
+    if (nlong > 0)
+        k_map_long<<<(unsigned)std::min<int64_t>(nlong, 65535), TPB, 0, st>>>(M.lrp, M.lrow, M.row_ptr, nlong, dmap);
+    if (nslice > 0)
+        k_map_slices<<<(unsigned)std::min<int64_t>(nslice, 1 << 20), 64, 0, st>>>(M.sbase, M.srow, M.row_ptr, nslice,
+                                                                                 SW, dmap);
+    IdxPack src{};
+    IdxPackW dst{};
+    for (int j = 0; j < nm1; ++j) {
+        HQ_TRY(dalloc(c, (void **)&M.hidx[j], (total + 16) * sizeof(int32_t)));
+        src.p[j] = M.oidx[j];
+        dst.p[j] = M.hidx[j];
+    }
+    HQ_TRY(dalloc(c, &M.hvals, (total + 16) * sizeof(T)));
+    k_hyb_gather<T><<<std::min(grid_for(total + 16), c->num_sms * 8), TPB, 0, st>>>(
+        src, dst, nm1, dmap, total + 16, (const T *)M.vals, (T *)M.hvals);
     HQ_TRY(up(&M.item_s, is));
     HQ_TRY(up(&M.item_e, ie));
     HQ_TRY(up(&M.item_aux, ia));
