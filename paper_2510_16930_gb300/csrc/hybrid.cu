@@ -20,7 +20,7 @@
 //    its pieces to per-task slots that k_span_fix adds in task order.
 //  - Slice tasks: lane group g owns row g of the slice, so no cross-group sum
 //    is needed; padding entries have value 0 and gather row 0.
-// Each window of the index/value streams (HY_W elements) is staged in shared
+// Each window of the index/value streams (hw elements) is staged in shared
 // memory by TMA bulk copies completing on an mbarrier, double buffered across
 // the warp's windows; all waits are bounded.
 #include <cuda.h>
@@ -35,8 +35,11 @@ namespace hoqri {
 namespace {
 
 constexpr int HY_WARPS = 8;
-constexpr int HY_W = 128;           // staged elements per window (multiple of 32)
-constexpr int HY_WB = HY_W + 8;     // floats per staged array
+// staged elements per window (multiple of 32): as large as two blocks per SM
+// allow (512 for three index arrays, 256 for four); larger windows mean fewer
+// window turns (waits, descriptor updates, restarts of the software pipeline)
+constexpr int HY_W_MAX = 512;
+constexpr int HY_NMETA = 2;         // index/value windows per warp: the next one loads during this one
 constexpr size_t HY_SMEM_CAP = 200 * 1024;
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -91,7 +94,8 @@ struct HybArgs {
     int64_t nitem, nitem_long;
     int64_t ipw, nrange;                   // items per warp range, number of ranges
     int bar_off, gs_off, w_off, w_stride;  // shared memory layout (bytes)
-    int meta_bytes;                        // one staged array of a window (HY_WB floats)
+    int meta_bytes;                        // one staged array of a window (hw + 8 floats)
+    int hw;                                // elements per window
     const float *Ulsplit;                  // last other factor as BF16 (hi | lo) rows, same bytes per row
     const float *Gn;  // [Kn][Pm]
     float *A;
@@ -267,29 +271,34 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
         if (item < iend) {
             wv.p0 = a.item_s[item];
             wv.te = a.item_e[item];
-            wv.len = (int)min((int64_t)HY_W, wv.te - wv.p0);
+            wv.len = (int)min((int64_t)a.hw, wv.te - wv.p0);
         }
         return wv;
     };
     auto next_win = [&](const Win &wv) -> Win {
         if (wv.len == 0) return wv;
-        const int64_t np0 = wv.p0 + HY_W;
-        if (np0 < wv.te) return Win{wv.it, np0, wv.te, (int)min((int64_t)HY_W, wv.te - np0), false};
+        const int64_t np0 = wv.p0 + a.hw;
+        if (np0 < wv.te) return Win{wv.it, np0, wv.te, (int)min((int64_t)a.hw, wv.te - np0), false};
         return item_win(next_item(wv.it));
     };
     Win W0 = item_win(PART == 0 ? r0 : a.nitem_long + gw);
     Win W1 = next_win(W0);
-    int issued = 0;  // windows whose streams were requested (buffer = window index mod 3)
+    int issued = 0;  // windows whose streams were requested (buffer = window index mod HY_NMETA)
     if (W0.len > 0) issue_meta(W0.p0, W0.p0 + W0.len, 0), ++issued;
-    if (W1.len > 0) issue_meta(W1.p0, W1.p0 + W1.len, 1), ++issued;
+    if (HY_NMETA == 3 && W1.len > 0) issue_meta(W1.p0, W1.p0 + W1.len, 1), ++issued;
     int64_t j = 0;
     int64_t jc = -1, crs = 0, cre = 0;  // cached bounds (lrp or sbase) of row / slice jc
     bool carry = false;  // a long row continues from the previous item of this range
-    int b0 = 0, b1 = 1, b2 = 2;  // meta buffers of windows mk, mk+1, mk+2
+    int b0 = 0, b1 = 1, b2 = 2;  // meta buffers of windows mk, mk+1 (, mk+2)
     while (W0.len > 0) {
-        const Win W2 = next_win(W1);
-        if (W2.len > 0) issue_meta(W2.p0, W2.p0 + W2.len, b2), ++issued;
-        if (!mbar_wait(mbar + b0, (uint32_t)((mk / 3) & 1), a.err)) {
+        Win W2 = W1;
+        if (HY_NMETA == 3) {
+            W2 = next_win(W1);
+            if (W2.len > 0) issue_meta(W2.p0, W2.p0 + W2.len, b2), ++issued;
+        } else if (W1.len > 0) {
+            issue_meta(W1.p0, W1.p0 + W1.len, b1), ++issued;
+        }
+        if (!mbar_wait(mbar + b0, (uint32_t)((mk / HY_NMETA) & 1), a.err)) {
             ok = false;
             break;
         }
@@ -524,18 +533,26 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
             }
         }
         __syncwarp();  // every lane is done with window mk's buffer before it is refilled
-        W0 = W1;
-        W1 = W2;
-        const int bt = b0;
-        b0 = b1;
-        b1 = b2;
-        b2 = bt;
+        if (HY_NMETA == 3) {
+            W0 = W1;
+            W1 = W2;
+            const int bt = b0;
+            b0 = b1;
+            b1 = b2;
+            b2 = bt;
+        } else {
+            W0 = W1;
+            W1 = next_win(W1);
+            b0 ^= 1;
+            b1 ^= 1;
+        }
         ++mk;
     }
     if (!ok) {
         // a window's copy never completed: bounded waits for this warp's requested
         // windows that were not consumed, then leave
-        for (int wq = mk; wq < issued; ++wq) mbar_wait(mbar + wq % 3, (uint32_t)((wq / 3) & 1), nullptr);
+        for (int wq = mk; wq < issued; ++wq)
+            mbar_wait(mbar + wq % HY_NMETA, (uint32_t)((wq / HY_NMETA) & 1), nullptr);
     }
 }
 
@@ -694,6 +711,7 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
 
 struct HybLaunch {
     size_t smem = 0;
+    int hw = 0;
     int bar_off = 0, gs_off = 0, w_off = 0, w_stride = 0, meta_bytes = 0;
     int MT = 0, NT = 0;  // tensor-core tiles of the long rows (0: FP32 FMA tiles)
 };
@@ -726,12 +744,13 @@ HybLaunch hyb_launch(const hoqri_ctx *c, int n, const FastTile &p) {
     HybLaunch L;
     const int narr = p.nm1 + 1;
     mix_shape(c, n, p, &L.MT, &L.NT);
-    // shared memory: three index/value windows per warp and their barriers
-    L.meta_bytes = HY_WB * 4;
+    // shared memory: HY_NMETA index/value windows per warp and their barriers
+    L.hw = narr == 3 ? HY_W_MAX : HY_W_MAX / 2;
+    L.meta_bytes = (L.hw + 8) * 4;
     L.bar_off = 0;
-    L.gs_off = al128(HY_WARPS * 3 * 8);
+    L.gs_off = al128(HY_WARPS * 3 * 8);  // three barriers per warp (at most HY_NMETA used)
     L.w_off = L.gs_off;
-    L.w_stride = al128(3 * narr * L.meta_bytes);
+    L.w_stride = al128(HY_NMETA * narr * L.meta_bytes);
     L.smem = (size_t)L.w_off + (size_t)HY_WARPS * L.w_stride;
     return L;
 }
@@ -836,6 +855,7 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.w_off = L.w_off;
     a.w_stride = L.w_stride;
     a.meta_bytes = L.meta_bytes;
+    a.hw = L.hw;
     {
         int j = 0;
         const float *Uo[3] = {nullptr, nullptr, nullptr};
