@@ -488,15 +488,19 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
         sbase[j + 1] = sbase[j] + ((SW * L + 3) & ~(int64_t)3);
     }
     const int64_t total = sbase[nslice];
-    // work items: long tasks of T8 elements, then runs of slices of about T8 elements
+    // work items: the long part in items of TL elements (at least T8, and at
+    // least an equal share per warp of the pass, so a warp's range is one item
+    // and its windows run on across the rows of the range), then runs of slices
+    const int64_t W = (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8;
+    const int64_t TL = std::max<int64_t>(T8, ((total_long + W - 1) / W + 31) & ~(int64_t)31);
     std::vector<int64_t> is, ie;
     std::vector<int32_t> ia, span;
     {
         int64_t j = 0;
-        for (int64_t t0 = 0; t0 < total_long; t0 += T8) {
+        for (int64_t t0 = 0; t0 < total_long; t0 += TL) {
             while (j + 1 < nlong && lrp[j + 1] <= t0) ++j;
             is.push_back(t0);
-            ie.push_back(std::min(t0 + T8, total_long));
+            ie.push_back(std::min(t0 + TL, total_long));
             ia.push_back((int32_t)j);
         }
     }
@@ -525,11 +529,10 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     // so a long row crossing items inside a range carries its partial sum; a long
     // row crossing a range boundary is completed from per-range pieces.  Slice
     // items are dealt to the warps in turn.
-    const int64_t W = (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8;
     const int64_t ipw = std::max<int64_t>(1, (nitem_long + W - 1) / W);
     const int64_t nrange = std::max<int64_t>(1, (nitem_long + ipw - 1) / ipw);
     for (int64_t jj = 0; jj < nlong; ++jj) {
-        const int64_t ta = lrp[jj] / T8, tb = (lrp[jj + 1] - 1) / T8;
+        const int64_t ta = lrp[jj] / TL, tb = (lrp[jj + 1] - 1) / TL;
         const int64_t ra = ta / ipw, rb = tb / ipw;
         if (ra != rb) {
             span.push_back((int32_t)jj);
