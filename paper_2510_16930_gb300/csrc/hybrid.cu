@@ -709,6 +709,102 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
     }
 }
 
+// A(row_id[r], :) = G_(n) y_r for KN = K_n in {4, 8, 16, 32}: thread owns 4
+// consecutive rows x all KN columns; G_(n) is staged transposed ([e][kn]) in
+// shared memory and read as broadcasts, the rows of Y as 16-byte loads.
+template <int KN>
+__global__ void __launch_bounds__(256) k_a_from_y2(const float *Y, const float *Gn, const int32_t *row_id, int64_t R,
+                                                   int Pm, float *A) {
+    extern __shared__ __align__(16) float Gt[];  // [Pm][KN]
+    for (int t = threadIdx.x; t < Pm * KN; t += blockDim.x) {
+        const int e = t / KN, k = t - e * KN;
+        Gt[t] = Gn[(size_t)k * Pm + e];
+    }
+    __syncthreads();
+    constexpr int RT = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * RT;
+    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * RT; r0 < R; r0 += stride) {
+        float2 acc[RT][KN / 2];
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int k = 0; k < KN / 2; ++k) acc[i][k] = make_float2(0.f, 0.f);
+        const float *yr[RT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i) yr[i] = Y + (size_t)min(r0 + i, R - 1) * Pm;
+        for (int e = 0; e < Pm; e += 4) {
+            float4 yv[RT];
+#pragma unroll
+            for (int i = 0; i < RT; ++i) yv[i] = __ldg(reinterpret_cast<const float4 *>(yr[i] + e));
+#pragma unroll
+            for (int ee = 0; ee < 4; ++ee) {
+                const float2 *g2 = reinterpret_cast<const float2 *>(Gt + (size_t)(e + ee) * KN);
+#pragma unroll
+                for (int k = 0; k < KN / 2; ++k) {
+                    const float2 g = g2[k];
+#pragma unroll
+                    for (int i = 0; i < RT; ++i) {
+                        const float yy = ee == 0 ? yv[i].x : (ee == 1 ? yv[i].y : (ee == 2 ? yv[i].z : yv[i].w));
+                        acc[i][k] = __ffma2_rn(make_float2(yy, yy), g, acc[i][k]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            if (r0 + i >= R) break;
+            float2 *arow = reinterpret_cast<float2 *>(A + (size_t)row_id[r0 + i] * KN);
+#pragma unroll
+            for (int k = 0; k < KN / 2; ++k) arow[k] = acc[i][k];
+        }
+    }
+}
+
+// CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) Y[r][e] for KN in
+// {4, 8, 16, 32} and P_{-n} <= 1024: Pm/4 threads cover a row (4 columns of e
+// each, all KN rows of G), the block's row groups take every ng-th row of the
+// CTA's range, and the groups are added in group order at the end.
+template <int KN>
+__global__ void __launch_bounds__(256) k_core_from_y2(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
+                                                      int Pm, int64_t rpb, float *cpart) {
+    extern __shared__ __align__(16) float red[];  // [ng][KN * Pm]
+    const int tpr = Pm >> 2;
+    const int ng = blockDim.x / tpr;
+    const int gi = threadIdx.x / tpr, eq = threadIdx.x - gi * tpr;
+    const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(r0 + rpb, R);
+    float4 acc[KN];
+#pragma unroll
+    for (int k = 0; k < KN; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (gi < ng) {
+        for (int64_t r = r0 + gi; r < r1; r += ng) {
+            const float4 y = __ldg(reinterpret_cast<const float4 *>(Y + (size_t)r * Pm) + eq);
+            const float4 *u4 = reinterpret_cast<const float4 *>(Un + (size_t)row_id[r] * KN);
+#pragma unroll
+            for (int kq = 0; kq < KN / 4; ++kq) {
+                const float4 u = __ldg(u4 + kq);
+                const float uu[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float4 &a = acc[4 * kq + c];
+                    a.x = fmaf(uu[c], y.x, a.x);
+                    a.y = fmaf(uu[c], y.y, a.y);
+                    a.z = fmaf(uu[c], y.z, a.z);
+                    a.w = fmaf(uu[c], y.w, a.w);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < KN; ++k) reinterpret_cast<float4 *>(red + (size_t)gi * KN * Pm + (size_t)k * Pm)[eq] = acc[k];
+    }
+    __syncthreads();
+    const int KnPm = KN * Pm;
+    for (int p = threadIdx.x; p < KnPm; p += blockDim.x) {
+        float s = 0.f;
+        for (int q = 0; q < ng; ++q) s += red[(size_t)q * KnPm + p];
+        cpart[(size_t)blockIdx.x * KnPm + p] = s;
+    }
+}
+
 struct HybLaunch {
     size_t smem = 0;
     int hw = 0;
@@ -913,7 +1009,21 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
     const int EC = Pm < 32 ? Pm : 32;
     const size_t smem = ((size_t)EC * (RT + 4) + (size_t)EC * Knp) * sizeof(float);
     HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * Kn * sizeof(float), c->stream));
-    if (M.R > 0) {
+    if (M.R > 0 && (Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && (size_t)Pm * Kn * 4 <= 96 * 1024) {
+        const size_t sm2 = (size_t)Pm * Kn * sizeof(float);
+        const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, 256 * 4), (int64_t)c->num_sms * 4));
+#define HQ_AY(KV)                                                                                             \
+    if (Kn == KV) {                                                                                           \
+        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
+        k_a_from_y2<KV><<<g2, 256, sm2, c->stream>>>(c->Y, Gn, M.row_id, M.R, Pm, A_out);                   \
+    }
+        HQ_AY(4)
+        HQ_AY(8)
+        HQ_AY(16)
+        HQ_AY(32)
+#undef HQ_AY
+        c->nlaunch++;
+    } else if (M.R > 0) {
         HQ_CUDA(cudaFuncSetAttribute(k_a_from_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, RT), (int64_t)c->num_sms * 4));
         k_a_from_y<<<grid, 256, smem, c->stream>>>(c->Y, Gn, M.row_id, M.R, Kn, Knp, Pm, RT, A_out);
@@ -934,9 +1044,25 @@ hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
                                                                 (int64_t)c->num_sms * 2));
     const int64_t rpb = ceil_div(std::max<int64_t>(R, 1), grid);
-    const size_t smem = (size_t)64 * Knp * sizeof(float);
-    k_core_from_y<<<grid, 256, smem, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Kn, Knp, Pm, rpb,
-                                                  (float *)c->core_part);
+    if ((Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && Pm <= 1024 &&
+        (size_t)(256 / (Pm / 4)) * Kn * Pm * 4 <= 200 * 1024) {
+        const size_t sm2 = (size_t)(256 / (Pm / 4)) * Kn * Pm * sizeof(float);
+#define HQ_CY(KV)                                                                                                \
+    if (Kn == KV) {                                                                                              \
+        HQ_CUDA(cudaFuncSetAttribute(k_core_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
+        k_core_from_y2<KV><<<grid, 256, sm2, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Pm, rpb,    \
+                                                          (float *)c->core_part);                                \
+    }
+        HQ_CY(4)
+        HQ_CY(8)
+        HQ_CY(16)
+        HQ_CY(32)
+#undef HQ_CY
+    } else {
+        const size_t smem = (size_t)64 * Knp * sizeof(float);
+        k_core_from_y<<<grid, 256, smem, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Kn, Knp, Pm, rpb,
+                                                      (float *)c->core_part);
+    }
     c->nlaunch++;
     HQ_CUDA(cudaGetLastError());
     *nblk = grid;
