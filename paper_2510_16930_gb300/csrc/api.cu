@@ -130,6 +130,7 @@ static void destroy_impl(hoqri_ctx *c) {
     dfree(c->Y, st);
     dfree(c->ypart, st);
     dfree(c->usplit, st);
+    dfree(c->claim, st);
     cudaGetLastError();
     delete c;
 }

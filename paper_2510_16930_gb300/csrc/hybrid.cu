@@ -103,6 +103,7 @@ struct HybArgs {
     float *apart;  // [nitem_long][2][Kn]
     float *ypart;  // [nitem_long][2][Pm]
     int32_t *err;
+    unsigned long long *claim;  // slice items handed out so far (part 1 takes them dynamically)
 };
 
 // ---- split-BF16 tensor-core helpers (legacy warp-level mma.sync: the per-row
@@ -163,7 +164,6 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
     __syncthreads();
 
     const int64_t gw = (int64_t)blockIdx.x * HY_WARPS + w;
-    const int64_t nw = (int64_t)gridDim.x * HY_WARPS;
 
     // stage the index and value streams of window [p0, p1) into meta buffer `buf`
     auto issue_meta = [&](int64_t p0, int64_t p1, int buf) {
@@ -255,7 +255,16 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
     const int64_t r0 = PART == 0 ? rg * a.ipw : 0;
     const int64_t r1 = PART == 0 ? (rg < a.nrange ? min(r0 + a.ipw, a.nitem_long) : r0) : 0;
     const int64_t iend = PART == 0 ? r1 : a.nitem;
-    auto next_item = [&](int64_t cur) -> int64_t { return PART == 0 ? cur + 1 : cur + nw; };
+    // part 1: a warp claims its next slice item from a device counter, so warps
+    // that finish early take more items (the item a row is computed in does not
+    // change its arithmetic, so results stay the same from run to run)
+    auto claim_slice = [&]() -> int64_t {
+        unsigned long long v = 0;
+        if (lane == 0) v = atomicAdd(a.claim, 1ull);
+        v = __shfl_sync(0xffffffffu, v, 0);
+        return a.nitem_long + (int64_t)v;
+    };
+    auto next_item = [&](int64_t cur) -> int64_t { return PART == 0 ? cur + 1 : claim_slice(); };
     const int64_t lfirst = (PART == 0 && r0 < r1) ? a.item_aux[r0] : -1;
     const int64_t lbeg = (PART == 0 && r0 < r1) ? a.item_s[r0] : 0;
     const int64_t lend = (PART == 0 && r0 < r1) ? a.item_e[r1 - 1] : 0;
@@ -281,7 +290,7 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
         if (np0 < wv.te) return Win{wv.it, np0, wv.te, (int)min((int64_t)a.hw, wv.te - np0), false};
         return item_win(next_item(wv.it));
     };
-    Win W0 = item_win(PART == 0 ? r0 : a.nitem_long + gw);
+    Win W0 = item_win(PART == 0 ? r0 : claim_slice());
     Win W1 = next_win(W0);
     int issued = 0;  // windows whose streams were requested (buffer = window index mod HY_NMETA)
     if (W0.len > 0) issue_meta(W0.p0, W0.p0 + W0.len, 0), ++issued;
@@ -880,6 +889,7 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
             c->nlaunch++;                                                                                    \
         }                                                                                                    \
         if (a.nitem > a.nitem_long) {                                                                        \
+            HQ_CUDA(cudaMemsetAsync(a.claim, 0, sizeof(unsigned long long), c->stream));                     \
             k1<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                               \
             c->nlaunch++;                                                                                    \
         }                                                                                                    \
@@ -984,6 +994,7 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     a.Y = c->Y;
     a.ypart = c->ypart;
     a.err = c->dflag + 2;
+    a.claim = c->claim;
     cudaEvent_t e0 = nullptr;
     HQ_TRY(prof_begin(c, 3, &e0));
     HQ_TRY(p.nm1 == 2 ? launch_hyb_nm1<2>(c, n, p, a, L) : launch_hyb_nm1<3>(c, n, p, a, L));

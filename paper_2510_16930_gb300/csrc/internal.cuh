@@ -106,6 +106,7 @@ struct hoqri_ctx {
     size_t rsize = 4;                   // sizeof(real)
     bool mix = false;                   // HOQRI_BF16X3: FP32 storage, split-BF16 tensor-core long rows
     void *usplit = nullptr;             // BF16 (hi | lo) rows of one factor (tensor-core B operand)
+    unsigned long long *claim = nullptr;  // work counter of the slice launch of the hybrid pass
     int device = 0;
     int num_sms = 0;
     cudaStream_t stream = nullptr;

@@ -990,6 +990,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
         c->ypart_bytes = ypb;
     }
     HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((c->P + 31) / 32 + 1) * sizeof(double)));
+    HQ_TRY(dalloc(c, (void **)&c->claim, sizeof(unsigned long long)));
     if (c->mix && c->Y) {
         int64_t sb = 0;
         for (int m = 0; m < c->N; ++m) sb = std::max<int64_t>(sb, c->dims[m] * c->K[m] * 4);
