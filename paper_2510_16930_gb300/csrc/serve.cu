@@ -11,9 +11,13 @@
 // hoqri_server_take copies them out and frees its memory, so a request that
 // arrives while others run is admitted as soon as memory and a slot free up.
 // Every request's arithmetic is that of a lone context, in the same order, so
-// its results do not depend on the mix it ran in.
+// its results do not depend on the mix it ran in.  The set-up of an admitted
+// request (sorting, layouts, graph capture: host work between short device
+// steps) runs on a worker thread, so several requests are set up at once
+// while the scheduler keeps polling.
 #include <algorithm>
 #include <chrono>
+#include <future>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -51,6 +55,8 @@ struct Req {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     hoqri_ctx *ctx = nullptr;
+    std::future<hoqri_status> setup;  // admission in progress on a worker thread
+    bool admitting = false;
 };
 
 }  // namespace
@@ -102,6 +108,12 @@ hoqri_status srv_fail(hoqri_status s, const std::string &m) {
 }
 
 void release(hoqri_server *s, Req *r) {
+    if (r->admitting) {  // a set-up still in flight: let it finish first
+        r->setup.wait();
+        r->admitting = false;
+        s->in_use -= r->est_bytes;
+        s->in_use += r->bytes;
+    }
     if (r->ctx) {
         hoqri_destroy(r->ctx);
         r->ctx = nullptr;
@@ -114,12 +126,14 @@ void release(hoqri_server *s, Req *r) {
     r->bytes = 0;
 }
 
-// admit: stream, context (stream-ordered allocations), all sweeps queued
-hoqri_status admit(hoqri_server *s, Req *r) {
+// admission work (runs on a worker thread): stream, context (stream-ordered
+// allocations), all sweeps queued, end event recorded.  Touches only r.
+hoqri_status admit_work(Req *r) {
     if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->done, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        return srv_fail(HOQRI_ERR_CUDA, "server: stream or event creation failed");
+        r->error = "server: stream or event creation failed";
+        return HOQRI_ERR_CUDA;
     }
     const void *idx_ptrs[HOQRI_MAXN];
     for (int n = 0; n < r->N; ++n) idx_ptrs[n] = r->idx[n];
@@ -134,22 +148,30 @@ hoqri_status admit(hoqri_server *s, Req *r) {
     }
     if (st == HOQRI_OK && cudaEventRecord(r->done, r->stream) != cudaSuccess) {
         cudaGetLastError();
-        st = srv_fail(HOQRI_ERR_CUDA, "server: event record failed");
+        set_error("server: event record failed");
+        st = HOQRI_ERR_CUDA;
     }
+    if (st != HOQRI_OK) r->error = hoqri_last_error();
+    return st;
+}
+
+// a finished admission: RUNNING, or FAILED with its memory released
+void admit_done(hoqri_server *s, Req *r) {
+    const hoqri_status st = r->setup.get();
+    r->admitting = false;
     r->t_admit = now_s();
+    s->in_use -= r->est_bytes;  // the estimate charged at dispatch ...
     if (st != HOQRI_OK) {
-        r->error = hoqri_last_error();
         r->status = st;
         r->state = HOQRI_REQ_FAILED;
         r->t_done = r->t_admit;
-        r->bytes = 0;  // not yet counted in the server's bytes in use
+        r->bytes = 0;
         release(s, r);
-        return HOQRI_OK;  // the request failed, not the server
+        --s->active;
+        return;
     }
-    s->in_use += r->bytes;
+    s->in_use += r->bytes;  // ... is replaced by the context's actual bytes
     r->state = HOQRI_REQ_RUNNING;
-    ++s->active;
-    return HOQRI_OK;
 }
 
 }  // namespace
@@ -201,10 +223,15 @@ hoqri_status hoqri_server_submit(hoqri_server *s, const hoqri_request *q, int64_
 
 hoqri_status hoqri_server_step(hoqri_server *s, int32_t *n_running, int32_t *n_queued) {
     if (!s) return srv_fail(HOQRI_ERR_INVALID, "hoqri_server_step: NULL server");
+    // admissions whose set-up finished on their worker thread
+    for (auto &kv : s->reqs) {
+        Req *r = kv.second.get();
+        if (r->admitting && r->setup.wait_for(std::chrono::seconds(0)) == std::future_status::ready) admit_done(s, r);
+    }
     // finished requests: their event has completed (non-blocking query)
     for (auto &kv : s->reqs) {
         Req *r = kv.second.get();
-        if (r->state != HOQRI_REQ_RUNNING) continue;
+        if (r->state != HOQRI_REQ_RUNNING || r->admitting) continue;
         const cudaError_t e = cudaEventQuery(r->done);
         if (e == cudaErrorNotReady) continue;
         r->t_done = now_s();
@@ -219,12 +246,17 @@ hoqri_status hoqri_server_step(hoqri_server *s, int32_t *n_running, int32_t *n_q
             r->state = HOQRI_REQ_DONE;
         }
     }
-    // admission in arrival order: the head waits until memory and a slot are free
+    // admission in arrival order: the head waits until memory and a slot are free;
+    // its set-up starts on a worker thread (the estimate is charged meanwhile)
     while (!s->queue.empty() && s->active < s->max_active) {
         Req *r = s->reqs[s->queue.front()].get();
         if (s->in_use + r->est_bytes > s->budget) break;
         s->queue.pop_front();
-        HQ_TRY(admit(s, r));
+        s->in_use += r->est_bytes;
+        ++s->active;
+        r->admitting = true;
+        r->state = HOQRI_REQ_RUNNING;  // reported as running from dispatch on
+        r->setup = std::async(std::launch::async, admit_work, r);
     }
     if (n_running) *n_running = s->active;
     if (n_queued) *n_queued = (int32_t)s->queue.size();
