@@ -158,11 +158,15 @@ def alg_bytes_per_pass(dims, ranks, rows, nnz, n, rsize):
     return nnz * ((N - 1) * 4 + rsize) + rows[n] * 12 + dims[n] * ranks[n] * rsize
 
 
+# the sources that decide the nonzero-stream kernel's DRAM traffic: the kernel
+# itself, the layout it reads (built in setup.cu) and the shared definitions
+TRAFFIC_SOURCES = ("hybrid.cu", "setup.cu", "internal.cuh")
+
+
 def source_hash():
     h = hashlib.sha256()
-    for f in sorted(os.listdir(os.path.join(ROOT, "paper_2510_16930_gb300", "csrc"))):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(ROOT, "paper_2510_16930_gb300", "csrc", f), "rb").read())
+    for f in TRAFFIC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2510_16930_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -71,9 +71,10 @@ typedef enum {
 
 typedef struct {
     int32_t prec;       /* hoqri_precision */
-    int32_t qr_kind;    /* 0: CholeskyQR2 in FP64, Householder when Cholesky breaks
-                           down; 1: Householder only; 2: CholeskyQR2, breakdown is an
-                           error (HOQRI_ERR_QR_BREAKDOWN) */
+    int32_t qr_kind;    /* 0: CholeskyQR2 in FP64 (shifted CholeskyQR3 when the first
+                           pivot is not clearly positive), Householder when that breaks
+                           down too; 1: Householder only; 2: as 0, but a breakdown
+                           is an error (HOQRI_ERR_QR_BREAKDOWN) */
     int32_t chunk_nnz;  /* nonzeros per warp task; 0 = chosen by the library */
     int32_t autotune;   /* 1: at create, time candidate layouts of the nonzero-stream
                            pass per mode (long-row threshold, work-item size) and keep
@@ -125,8 +126,8 @@ HOQRI_API hoqri_status hoqri_core(hoqri_ctx *ctx, void *G_out);
 HOQRI_API hoqri_status hoqri_ttmctc(hoqri_ctx *ctx, int32_t mode, void *A_out);
 
 /* U_out = orthonormal basis of the columns of A_in (Alg. 2, the QR step): thin QR
- * with diag(R) > 0 by CholeskyQR2 in FP64 (Householder on breakdown, per
- * qr_kind).  A_in: I_mode x K_mode reals; U_out may equal A_in.  The factors of
+ * with diag(R) > 0 by CholeskyQR2 in FP64 (shifted CholeskyQR3 for an
+ * ill-conditioned A_in, Householder on breakdown, per qr_kind).  A_in: I_mode x K_mode reals; U_out may equal A_in.  The factors of
  * the context are not changed. */
 HOQRI_API hoqri_status hoqri_orthonormalize(hoqri_ctx *ctx, int32_t mode, const void *A_in, void *U_out);
 
@@ -192,8 +193,8 @@ HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
  *           overlapping it
  *   stream  cudaStream_t all work is ordered on (NULL: legacy default stream)
  * Scratch: one file-scope device array of HOQRI_NOALLOC_SCRATCH_BYTES per
- * device (Gram partials of at most 160 blocks, R^{-1} and two flags).  Every
- * call sets its two flags to zero itself (cudaMemsetAsync on the stream);
+ * device (Gram partials of at most 160 blocks, R^{-1} and four flags).  Every
+ * call sets its flags to zero itself (cudaMemsetAsync on the stream);
  * the partials and R^{-1} are fully written before they are read, so nothing
  * needs to start at zero.  Its address is looked up with cudaGetSymbolAddress
  * on the first call made on each device (cached afterwards); that first call
@@ -203,9 +204,9 @@ HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
  * The call waits for the stream to finish, since it reads the breakdown flag.
  * Errors: HOQRI_ERR_INVALID for a precision other than the two above, K out of
  * range (the message names the limit), I < K, host or overlapping buffers;
- * HOQRI_ERR_QR_BREAKDOWN when a Cholesky pivot is not clearly positive (A_in
- * rank deficient or too ill conditioned; there is no Householder fallback
- * here, U_out is then unspecified); HOQRI_ERR_CUDA on a CUDA failure. */
+ * HOQRI_ERR_QR_BREAKDOWN when a Cholesky pivot is not clearly positive after
+ * the shifted first pass (A_in rank deficient; there is no Householder
+ * fallback here, U_out is then unspecified); HOQRI_ERR_CUDA on a CUDA failure. */
 #define HOQRI_NOALLOC_MAXK 32
 #define HOQRI_NOALLOC_SCRATCH_BYTES (160 * 528 * 8 + 32 * 32 * 8 + 256)
 HOQRI_API hoqri_status hoqri_orthonormalize_noalloc(int32_t prec, int64_t I, int32_t K, const void *A_in,

@@ -120,7 +120,8 @@ struct hoqri_ctx {
     double *dnorm = nullptr;
     int64_t dnorm_slots = 0;
     int32_t *dflag = nullptr;           // [0] QR state of the current QR, [1] breakdown count,
-                                        // [2] device wait ran out (error)
+                                        // [2] device wait ran out (error), [3] the current
+                                        // QR's first pass was shifted
     // scratch of the passes (partials); see passes.cu
     void *core_part = nullptr;          // per-CTA core partials
     int64_t core_part_bytes = 0;

@@ -3,15 +3,24 @@
 // CholeskyQR2 in FP64: W = A^T A (Gram, FP64 sums in a fixed order),
 // W = R^T R (Cholesky, one CTA), A <- A R^{-1}; then once more on the result.
 // Both R factors have a positive diagonal, so the result is the Q of the thin
-// QR with diag(R) > 0.  When a Cholesky pivot is not clearly positive (A is
-// rank deficient or too ill-conditioned for CholeskyQR), a one-CTA Householder
-// QR in FP64 produces Q instead (columns signed so diag(R) >= 0; zero pivot
-// columns are completed by the accumulated reflectors).  The decision is
-// taken on the device through a flag, so the sequence needs no host round trip
-// and can be captured in a CUDA graph:
-//   flag = 0  -> the CholeskyQR kernels run;
-//   flag = 1  -> breakdown seen; the Householder kernel runs and sets flag = 2;
-//   flag = 2  -> U is written; every later kernel of this QR returns at once.
+// QR with diag(R) > 0.  A_n = Y_(n) G_(n)^T with G_(n) = U_n^T Y_(n) squares
+// the conditioning of Y_(n), so a first pivot that is not clearly positive is
+// common on skewed data: then the first Cholesky is taken of W + s I instead
+// (shifted CholeskyQR3, Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa,
+// SIAM J. Sci. Comput. 42(1), 2020: s = 11 (m n + n (n + 1)) u ||A||^2, with
+// ||A||_F^2 = trace(W) for ||A||_2^2), which leaves A R^{-1} well enough
+// conditioned for the two unshifted passes that follow.  When a pivot of a
+// later pass is not clearly positive (A is rank deficient), a one-CTA
+// Householder QR in FP64 produces Q instead (columns signed so diag(R) >= 0;
+// zero pivot columns are completed by the accumulated reflectors).  The
+// decisions are taken on the device through flags, so the sequence needs no
+// host round trip and can be captured in a CUDA graph:
+//   flag[0] = 0  -> the CholeskyQR kernels run;
+//   flag[0] = 1  -> breakdown seen; the Householder kernel runs and sets 2;
+//   flag[0] = 2  -> U is written; every later kernel of this QR returns at once;
+//   flag[1]      -> breakdowns counted over the context's life;
+//   flag[3] = 1  -> the first pass was shifted: the third pass runs (else its
+//                   kernels return at once).
 #include <algorithm>
 #include <mutex>
 
@@ -25,11 +34,17 @@ constexpr int GRAM_TPB = 256;
 constexpr int GRAM_ROWS = 32;   // rows staged per step
 constexpr int MAX_GRAM_BLOCKS = 304;
 constexpr int HH_TPB = 1024;
+constexpr int QR_PASSES = 3;  // the third runs only after a shifted first pass
+
+// true when the kernels of this pass have nothing to do (see the flag states)
+__device__ __forceinline__ bool qr_skip(const int32_t *flag, int pass) {
+    return flag[0] != 0 || (pass == 2 && flag[3] == 0);
+}
 
 template <typename T>
 __global__ void __launch_bounds__(GRAM_TPB) k_gram_partial(const T *A, int64_t I, int K, int64_t rows_per_block,
-                                                           double *part, const int32_t *flag) {
-    if (*flag != 0) return;
+                                                           double *part, const int32_t *flag, int pass) {
+    if (qr_skip(flag, pass)) return;
     __shared__ double tile[GRAM_ROWS * HOQRI_MAXK];
     const int npairs = K * (K + 1) / 2;
     constexpr int MAXP = (HOQRI_MAXK * (HOQRI_MAXK + 1) / 2 + GRAM_TPB - 1) / GRAM_TPB;
@@ -89,19 +104,12 @@ __device__ __forceinline__ double rsqrt_fp64(double d) {
     return y;
 }
 
-// Sum of the Gram partials in block order, Cholesky W = R^T R, Rinv = R^{-1}.
-// The partial sums use all warps; the factorisation and the inverse run in
-// warp 0 (lane k holds column k), so the sequential pivots need no block
-// barrier.  R overwrites the upper triangle of W in place.
-__global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int K, double *Rinv, int32_t *flag) {
-    if (*flag != 0) return;
-    __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
-    __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j)
+// W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal):
+// thread per pair (coalesced across the threads for each block), eight
+// interleaved partial sums so eight loads are in flight, combined in a fixed
+// order (same result every run)
+__device__ void gram_sum(const double *part, int nblk, int K, double shift, double *W) {
     const int npairs = K * (K + 1) / 2;
-    // W(i, j) = sum of the block partials: thread per pair (coalesced across the
-    // threads for each block), eight interleaved partial sums so eight loads are
-    // in flight, combined in a fixed order (same result every run)
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
         double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int b = 0;
@@ -115,22 +123,25 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
             rem -= K - i;
             ++i;
         }
-        W[i * K + i + rem] = s;
+        W[i * K + i + rem] = rem == 0 ? s + shift : s;
     }
-    __syncthreads();
-    if (wid != 0) return;
+}
+
+// W = R^T R in place (R in the upper triangle), inv(j) = 1 / R(j, j); one warp,
+// lane k holds column k, so the sequential pivots need no block barrier.
+// Returns 1 when a pivot is not above 1e-14 max_j W(j, j).
+__device__ int chol_warp(double *W, double *inv, int K, int lane) {
     double dmax = 0.0;
     for (int i = 0; i < K; ++i) dmax = fmax(dmax, W[i * K + i]);
     const double tiny = 1e-14 * dmax;
-    int bad = !(dmax > 0.0);
-    for (int j = 0; j < K && !bad; ++j) {
+    if (!(dmax > 0.0)) return 1;
+    for (int j = 0; j < K; ++j) {
         // pivot: d = W(j,j) - sum_{i<j} R(i,j)^2, a lane-strided sum in fixed order
         double d = 0.0;
         for (int i = lane; i < j; i += 32) d += W[i * K + j] * W[i * K + j];
         for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
         d = W[j * K + j] - d;
-        bad = !(d > tiny);
-        if (bad) break;
+        if (!(d > tiny)) return 1;
         const double y = rsqrt_fp64(d);  // 1 / R(j, j)
         // row j of R: R(j,k) = (W(j,k) - sum_{i<j} R(i,j) R(i,k)) / R(j,j), lane per k
         for (int k = j + 1 + lane; k < K; k += 32) {
@@ -145,9 +156,48 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
         }
         __syncwarp();
     }
-    if (bad) {
+    return 0;
+}
+
+// Sum of the Gram partials, Cholesky W = R^T R (of W + s I after a breakdown in
+// the first pass), Rinv = R^{-1}.  The partial sums use all warps; the
+// factorisation and the inverse run in warp 0.  m = rows of A.
+__global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int K, int64_t m, double *Rinv,
+                                              int32_t *flag, int pass) {
+    if (qr_skip(flag, pass)) return;
+    __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
+    __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j)
+    __shared__ int s_bad;
+    __shared__ double s_shift;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    gram_sum(part, nblk, K, 0.0, W);
+    __syncthreads();
+    if (wid == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < K; ++i) tr += W[i * K + i];
+        const int bad = chol_warp(W, inv, K, lane);
         if (lane == 0) {
-            *flag = 1;
+            s_bad = bad;
+            s_shift = 11.0 * ((double)m * K + (double)K * (K + 1)) * 0x1p-53 * tr;
+        }
+    }
+    __syncthreads();
+    if (s_bad && pass == 0 && s_shift > 0.0) {
+        gram_sum(part, nblk, K, s_shift, W);
+        __syncthreads();
+        if (wid == 0) {
+            const int bad = chol_warp(W, inv, K, lane);
+            if (lane == 0) {
+                s_bad = bad;
+                if (!bad) flag[3] = 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (wid != 0) return;
+    if (s_bad) {
+        if (lane == 0) {
+            flag[0] = 1;
             flag[1] += 1;
         }
         return;
@@ -175,8 +225,8 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
 // are multiplied in FP32 (the factor is stored in FP32), FP64 rows in FP64.
 template <typename T, int KC>
 __global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const double *Rinv, T *out,
-                                                    const int32_t *flag) {
-    if (*flag != 0) return;
+                                                    const int32_t *flag, int pass) {
+    if (qr_skip(flag, pass)) return;
     __shared__ T Rs[KC * KC];
     for (int t = threadIdx.x; t < KC * KC; t += blockDim.x) Rs[t] = (T)Rinv[t];
     __syncthreads();
@@ -218,8 +268,8 @@ __global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const
 // any K <= 64: one thread per row, row kept in local memory
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, int K, const double *Rinv, T *out,
-                                                        const int32_t *flag) {
-    if (*flag != 0) return;
+                                                        const int32_t *flag, int pass) {
+    if (qr_skip(flag, pass)) return;
     __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
     __syncthreads();
@@ -235,20 +285,20 @@ __global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, i
 }
 
 template <typename T>
-void launch_apply(cudaStream_t st, const int32_t *flag, const T *A, int64_t I, int K, const double *Rinv, T *out,
-                  int grid) {
+void launch_apply(cudaStream_t st, const int32_t *flag, int pass, const T *A, int64_t I, int K, const double *Rinv,
+                  T *out, int grid) {
     // the fixed-width kernels move FP32 rows as 16-byte vectors: both buffers must be 16-byte aligned
     const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     if (!aligned) {
-        k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag);
+        k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag, pass);
         return;
     }
     switch (K) {
-        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
-        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
-        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
-        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag); break;
-        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag); break;
+        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
+        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
+        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
+        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
+        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag, pass); break;
     }
 }
 
@@ -368,7 +418,10 @@ __global__ void k_gauss(T *out, int64_t n, uint64_t seed, uint32_t stream_id) {
     }
 }
 
-__global__ void k_set_flag(int32_t *flag, int32_t v) { *flag = v; }
+__global__ void k_set_flag(int32_t *flag, int32_t v) {
+    flag[0] = v;
+    flag[3] = 0;
+}
 
 // one Gram block per SM at most (the FP64 multiply-adds need every SM; fewer
 // partials keep the Cholesky's reduction short)
@@ -387,15 +440,18 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     const int npairs = K * (K + 1) / 2;
     double *Rinv = c->qr_small;
     const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
-    // flag 0: CholeskyQR2; flag 1 (qr_kind 1): Householder from the start.  Set
-    // with a kernel, not a copy from host memory, so a captured graph replays it.
+    // flag 0: CholeskyQR2; flag 1 (qr_kind 1): Householder from the start; no
+    // shift yet.  Set with a kernel, not a copy from host memory, so a captured
+    // graph replays it.
     k_set_flag<<<1, 1, 0, st>>>(c->dflag, c->opt.qr_kind == 1 ? 1 : 0);
     c->nlaunch++;
-    for (int pass = 0; pass < 2; ++pass) {
-        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(A, I, K, rpb, c->qr_part, c->dflag);
-        k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, Rinv, c->dflag);
-        k_householder<T><<<1, HH_TPB, 0, st>>>(A, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
-        launch_apply<T>(st, c->dflag, A, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
+    // pass 0: A <- A R1^{-1}; pass 1: U = A R2^{-1}; pass 2 (after a shift): U <- U R3^{-1}
+    for (int pass = 0; pass < QR_PASSES; ++pass) {
+        T *src = pass < 2 ? A : U;
+        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, c->qr_part, c->dflag, pass);
+        k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, I, Rinv, c->dflag, pass);
+        k_householder<T><<<1, HH_TPB, 0, st>>>(src, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
+        launch_apply<T>(st, c->dflag, pass, src, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
         c->nlaunch += 4;
     }
     (void)npairs;
@@ -440,9 +496,10 @@ hoqri_status init_factors_seeded(hoqri_ctx *c) {
 }
 
 // ---- allocation-free CholeskyQR2 (hoqri_orthonormalize_noalloc): the same
-// Gram / Cholesky / apply kernels, with their scratch in one file-scope device
-// array instead of context buffers.  Layout: Gram partials of up to NA_BLOCKS
-// blocks | R^{-1} | flag[2] (on a 256-byte boundary).
+// Gram / Cholesky / apply kernels (shifted first pass included), with their
+// scratch in one file-scope device array instead of context buffers.  Layout:
+// Gram partials of up to NA_BLOCKS blocks | R^{-1} | flag[4] (on a 256-byte
+// boundary).
 namespace {
 
 constexpr int NA_BLOCKS = 160;
@@ -494,13 +551,14 @@ hoqri_status orthonormalize_noalloc_t(int64_t I, int K, const T *A, T *U, cudaSt
     const int nb = std::min(gram_blocks(I, sms), NA_BLOCKS);
     const int64_t rpb = ceil_div(I, nb);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)sms * 8));
-    HQ_CUDA(cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), st));
-    // pass 0: U = A R1^{-1}; pass 1: U = U R2^{-1} (in place, row by row)
-    for (int pass = 0; pass < 2; ++pass) {
+    HQ_CUDA(cudaMemsetAsync(flag, 0, 4 * sizeof(int32_t), st));
+    // pass 0: U = A R1^{-1}; passes 1 and 2 (the latter after a shifted first
+    // pass only): U = U R^{-1} in place, row by row
+    for (int pass = 0; pass < QR_PASSES; ++pass) {
         const T *src = pass == 0 ? A : U;
-        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, part, flag);
-        k_chol<<<1, 256, 0, st>>>(part, nb, K, Rinv, flag);
-        launch_apply<T>(st, flag, src, I, K, Rinv, U, grid);
+        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, part, flag, pass);
+        k_chol<<<1, 256, 0, st>>>(part, nb, K, I, Rinv, flag, pass);
+        launch_apply<T>(st, flag, pass, src, I, K, Rinv, U, grid);
     }
     HQ_CUDA(cudaGetLastError());
     int32_t f = 0;
@@ -508,7 +566,7 @@ hoqri_status orthonormalize_noalloc_t(int64_t I, int K, const T *A, T *U, cudaSt
     HQ_CUDA(cudaStreamSynchronize(st));
     if (f != 0) {
         set_error("hoqri_orthonormalize_noalloc: Cholesky breakdown (A is rank deficient or too ill conditioned "
-                  "for CholeskyQR2)");
+                  "for shifted CholeskyQR3)");
         return HOQRI_ERR_QR_BREAKDOWN;
     }
     return HOQRI_OK;

@@ -114,6 +114,43 @@ def test_orthonormalize_rank_deficient_falls_back(orc, prec):
     assert np.linalg.norm(A64 - Q @ (Q.T @ A64)) <= tol * np.linalg.norm(A64)
 
 
+def _ill_conditioned(kind, I, K, seed):
+    """I x K with a Cholesky pivot of its Gram below 1e-14 of the largest
+    diagonal entry: column scaling over 7.5 decades (Q itself stays well
+    determined), or singular values graded 1 .. 1e-9 in random directions
+    (kappa 1e9, beyond what unshifted CholeskyQR2 can take)."""
+    rng = np.random.default_rng(seed)
+    if kind == "scaled":
+        return rng.standard_normal((I, K)) * np.logspace(0, -7.5, K)[None, :]
+    sig = np.logspace(0, -9, K)
+    Q0, _ = np.linalg.qr(rng.standard_normal((I, K)))
+    V, _ = np.linalg.qr(rng.standard_normal((K, K)))
+    return (Q0 * sig[None, :]) @ V.T
+
+
+@pytest.mark.parametrize("prec,kind", [(FP64, "scaled"), (FP32, "scaled"), (FP64, "graded")])
+def test_orthonormalize_ill_conditioned_is_shifted_not_broken(orc, prec, kind):
+    """Unshifted CholeskyQR2 breaks down on these inputs; with qr_kind 2 (a
+    breakdown is an error) the call succeeds, so the shifted first pass
+    (shifted CholeskyQR3) produced Q.  Q is orthonormal, spans A, and equals the
+    oracle's Q to the conditioning of the problem (kappa u ~ 1e-7 for the graded
+    case)."""
+    I, K = 5000, 16
+    A = _ill_conditioned(kind, I, K, 31)
+    npdt = np.float64 if prec == FP64 else np.float32
+    A = A.astype(npdt)
+    X, U0 = _case((I, K, K), (K, K, K), 100, 5)
+    with Ctx((I, K, K), X.idx, X.vals.astype(npdt), [u.astype(npdt) for u in U0], prec, qr_kind=2) as c:
+        Q = c.orthonormalize(0, A)
+    A64 = A.astype(np.float64)
+    Q_ref, _, _ = orc.qr(A64)
+    tol_orth = 1e-13 if prec == FP64 else 1e-5
+    assert np.linalg.norm(Q.T @ Q - np.eye(K)) <= tol_orth
+    assert np.linalg.norm(A64 - Q @ (Q.T @ A64)) <= tol_orth * np.linalg.norm(A64)
+    tol_q = {("scaled", FP64): 1e-11, ("scaled", FP32): 2e-6 * K, ("graded", FP64): 1e-6}[(kind, prec)]
+    assert rel(Q, Q_ref) <= tol_q
+
+
 def test_hoqri_200cubed_fp64_matches_oracle(orc):
     """The 200^3, nnz 1e4, K = 5 workload, 10 iterations, FP64 throughout."""
     X, U0, cfg = inputs.make_config("c1")

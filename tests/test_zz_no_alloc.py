@@ -81,6 +81,20 @@ def test_noalloc_breakdown_then_recovers():
     assert rel(U, _context_result(B, hoqri.HOQRI_FP64)) <= TOL[hoqri.HOQRI_FP64]
 
 
+@pytest.mark.parametrize("prec", [hoqri.HOQRI_FP64, hoqri.HOQRI_FP32])
+def test_noalloc_ill_conditioned_takes_the_shifted_pass(prec):
+    """Columns scaled over 7.5 decades: unshifted CholeskyQR2 breaks down, the
+    shifted first pass does not; same U as the context's QR on the same input."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(17)
+    A = rng.standard_normal((4000, 16)) * np.logspace(0, -7.5, 16)[None, :]
+    if prec == hoqri.HOQRI_FP32:
+        A = A.astype(np.float32)
+    U, _ = _noalloc(torch, A, prec)
+    assert np.linalg.norm(U.T @ U - np.eye(16)) <= (1e-13 if prec == hoqri.HOQRI_FP64 else 1e-5)
+    assert rel(U, _context_result(A, prec)) <= TOL[prec]
+
+
 def test_noalloc_rejects_oversize_and_host_buffers():
     torch = pytest.importorskip("torch")
     A = torch.zeros((100, 33), dtype=torch.float64, device="cuda")
