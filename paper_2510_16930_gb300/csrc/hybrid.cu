@@ -718,50 +718,87 @@ __global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float
     }
 }
 
-// A(row_id[r], :) = G_(n) y_r for KN = K_n in {4, 8, 16, 32}: thread owns 4
-// consecutive rows x all KN columns; G_(n) is staged transposed ([e][kn]) in
-// shared memory and read as broadcasts, the rows of Y as 16-byte loads.
+// A(row_id[r], :) = G_(n) y_r for KN = K_n in {4, 8, 16, 32}: each CTA takes a
+// contiguous range of rows (equal ranges, one wave of CTAs), a thread two rows
+// (one for KN = 32) x all KN columns at a time.  G_(n) is staged transposed ([e][kn]) in shared
+// memory and read as broadcasts; the rows of Y stream in as 16-byte loads,
+// the next two vectors of each row issued before the current two are used,
+// so every thread keeps loads in flight while it multiplies (the kernel streams Y once and
+// is bound by HBM latency otherwise).
+constexpr int AY_EB = 2;
+
 template <int KN>
-__global__ void __launch_bounds__(256) k_a_from_y2(const float *Y, const float *Gn, const int32_t *row_id, int64_t R,
-                                                   int Pm, float *A) {
+__host__ __device__ constexpr int ay_rt() { return KN >= 32 ? 1 : 2; }  // rows per thread (KN = 32: registers)
+
+template <int KN, int AY_RT>
+__device__ __forceinline__ void ay_step(const float *Gt, int e, const float4 (&yv)[AY_RT],
+                                        float2 (&acc)[AY_RT][KN / 2]) {
+#pragma unroll
+    for (int ee = 0; ee < 4; ++ee) {
+        const float2 *g2 = reinterpret_cast<const float2 *>(Gt + (size_t)(e + ee) * KN);
+#pragma unroll
+        for (int k = 0; k < KN / 2; ++k) {
+            const float2 g = g2[k];
+#pragma unroll
+            for (int i = 0; i < AY_RT; ++i) {
+                const float yy = ee == 0 ? yv[i].x : (ee == 1 ? yv[i].y : (ee == 2 ? yv[i].z : yv[i].w));
+                acc[i][k] = __ffma2_rn(make_float2(yy, yy), g, acc[i][k]);
+            }
+        }
+    }
+}
+
+template <int KN>
+__global__ void __launch_bounds__(256, 2) k_a_from_y2(const float *Y, const float *Gn, const int32_t *row_id,
+                                                      int64_t R, int64_t rpb, int Pm, float *A) {
+    constexpr int AY_RT = ay_rt<KN>();
     extern __shared__ __align__(16) float Gt[];  // [Pm][KN]
     for (int t = threadIdx.x; t < Pm * KN; t += blockDim.x) {
         const int e = t / KN, k = t - e * KN;
         Gt[t] = Gn[(size_t)k * Pm + e];
     }
     __syncthreads();
-    constexpr int RT = 4;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * RT;
-    for (int64_t r0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * RT; r0 < R; r0 += stride) {
-        float2 acc[RT][KN / 2];
+    const int64_t rbeg = (int64_t)blockIdx.x * rpb, rend = min(rbeg + rpb, R);
+    const int nb = Pm / (4 * AY_EB);  // full batches of AY_EB vectors per row
+    for (int64_t r0 = rbeg + (int64_t)threadIdx.x * AY_RT; r0 < rend; r0 += (int64_t)blockDim.x * AY_RT) {
+        float2 acc[AY_RT][KN / 2];
 #pragma unroll
-        for (int i = 0; i < RT; ++i)
+        for (int i = 0; i < AY_RT; ++i)
 #pragma unroll
             for (int k = 0; k < KN / 2; ++k) acc[i][k] = make_float2(0.f, 0.f);
-        const float *yr[RT];
+        const float4 *yr[AY_RT];
 #pragma unroll
-        for (int i = 0; i < RT; ++i) yr[i] = Y + (size_t)min(r0 + i, R - 1) * Pm;
-        for (int e = 0; e < Pm; e += 4) {
-            float4 yv[RT];
+        for (int i = 0; i < AY_RT; ++i) yr[i] = reinterpret_cast<const float4 *>(Y + (size_t)min(r0 + i, rend - 1) * Pm);
+        float4 cur[AY_EB][AY_RT], nxt[AY_EB][AY_RT];
+        if (nb > 0) {
 #pragma unroll
-            for (int i = 0; i < RT; ++i) yv[i] = __ldg(reinterpret_cast<const float4 *>(yr[i] + e));
+            for (int b = 0; b < AY_EB; ++b)
 #pragma unroll
-            for (int ee = 0; ee < 4; ++ee) {
-                const float2 *g2 = reinterpret_cast<const float2 *>(Gt + (size_t)(e + ee) * KN);
+                for (int i = 0; i < AY_RT; ++i) cur[b][i] = __ldg(yr[i] + b);
+        }
+        for (int bt = 0; bt < nb; ++bt) {
+            if (bt + 1 < nb) {
 #pragma unroll
-                for (int k = 0; k < KN / 2; ++k) {
-                    const float2 g = g2[k];
+                for (int b = 0; b < AY_EB; ++b)
 #pragma unroll
-                    for (int i = 0; i < RT; ++i) {
-                        const float yy = ee == 0 ? yv[i].x : (ee == 1 ? yv[i].y : (ee == 2 ? yv[i].z : yv[i].w));
-                        acc[i][k] = __ffma2_rn(make_float2(yy, yy), g, acc[i][k]);
-                    }
-                }
+                    for (int i = 0; i < AY_RT; ++i) nxt[b][i] = __ldg(yr[i] + (bt + 1) * AY_EB + b);
             }
+#pragma unroll
+            for (int b = 0; b < AY_EB; ++b) ay_step<KN, AY_RT>(Gt, 4 * (bt * AY_EB + b), cur[b], acc);
+#pragma unroll
+            for (int b = 0; b < AY_EB; ++b)
+#pragma unroll
+                for (int i = 0; i < AY_RT; ++i) cur[b][i] = nxt[b][i];
+        }
+        for (int e = nb * 4 * AY_EB; e < Pm; e += 4) {
+            float4 yv[AY_RT];
+#pragma unroll
+            for (int i = 0; i < AY_RT; ++i) yv[i] = __ldg(yr[i] + (e >> 2));
+            ay_step<KN, AY_RT>(Gt, e, yv, acc);
         }
 #pragma unroll
-        for (int i = 0; i < RT; ++i) {
-            if (r0 + i >= R) break;
+        for (int i = 0; i < AY_RT; ++i) {
+            if (r0 + i >= rend) break;
             float2 *arow = reinterpret_cast<float2 *>(A + (size_t)row_id[r0 + i] * KN);
 #pragma unroll
             for (int k = 0; k < KN / 2; ++k) arow[k] = acc[i][k];
@@ -771,42 +808,99 @@ __global__ void __launch_bounds__(256) k_a_from_y2(const float *Y, const float *
 
 // CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) Y[r][e] for KN in
 // {4, 8, 16, 32} and P_{-n} <= 1024: Pm/4 threads cover a row (4 columns of e
-// each, all KN rows of G), the block's row groups take every ng-th row of the
-// CTA's range, and the groups are added in group order at the end.
-template <int KN>
+// each, all KN rows of G), the block's ng row groups take every ng-th row of
+// the CTA's range, and the groups are added in group order at the end.  The
+// U rows of CY_CH rows at a time are gathered into one of two shared-memory
+// buffers while the previous CY_CH rows are multiplied; each group loads the Y
+// vectors of the next RB of its rows before it multiplies the current RB
+// (RB = 4; 2 for KN = 32, whose 32 accumulator vectors leave fewer registers).
+constexpr int CY_CH = 128;
+
+template <int KN, int RB = (KN >= 32 ? 2 : 4)>
 __global__ void __launch_bounds__(256) k_core_from_y2(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
                                                       int Pm, int64_t rpb, float *cpart) {
-    extern __shared__ __align__(16) float red[];  // [ng][KN * Pm]
+    extern __shared__ __align__(16) float red[];  // [ng][KN * Pm] | Us [2][CY_CH][KN]
+    constexpr int UQ = KN / 4;                    // float4 per U row
+    constexpr int UPT = (CY_CH * UQ + 255) / 256;  // U vectors each thread stages per chunk
     const int tpr = Pm >> 2;
     const int ng = blockDim.x / tpr;
     const int gi = threadIdx.x / tpr, eq = threadIdx.x - gi * tpr;
+    const int KnPm = KN * Pm;
+    float4 *Us = reinterpret_cast<float4 *>(red + (size_t)ng * KnPm);
     const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(r0 + rpb, R);
     float4 acc[KN];
 #pragma unroll
     for (int k = 0; k < KN; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (gi < ng) {
-        for (int64_t r = r0 + gi; r < r1; r += ng) {
-            const float4 y = __ldg(reinterpret_cast<const float4 *>(Y + (size_t)r * Pm) + eq);
-            const float4 *u4 = reinterpret_cast<const float4 *>(Un + (size_t)row_id[r] * KN);
+    const float4 *Y4 = reinterpret_cast<const float4 *>(Y) + eq;
+    // U rows of the chunk starting at rb, as this thread's share of vectors
+    auto load_u = [&](int64_t rb, float4 (&u)[UPT]) {
+        const int nr = (int)min((int64_t)CY_CH, r1 - rb);
 #pragma unroll
-            for (int kq = 0; kq < KN / 4; ++kq) {
-                const float4 u = __ldg(u4 + kq);
-                const float uu[4] = {u.x, u.y, u.z, u.w};
+        for (int q = 0; q < UPT; ++q) {
+            const int t = threadIdx.x + q * 256;
+            const int rr = t / UQ, c = t - rr * UQ;
+            u[q] = (rb < r1 && rr < nr) ? __ldg(reinterpret_cast<const float4 *>(Un + (size_t)row_id[rb + rr] * KN) + c)
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    auto store_u = [&](int buf, const float4 (&u)[UPT]) {
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float4 &a = acc[4 * kq + c];
-                    a.x = fmaf(uu[c], y.x, a.x);
-                    a.y = fmaf(uu[c], y.y, a.y);
-                    a.z = fmaf(uu[c], y.z, a.z);
-                    a.w = fmaf(uu[c], y.w, a.w);
+        for (int q = 0; q < UPT; ++q) {
+            const int t = threadIdx.x + q * 256;
+            if (t < CY_CH * UQ) Us[buf * CY_CH * UQ + t] = u[q];
+        }
+    };
+    float4 un[UPT];
+    load_u(r0, un);
+    store_u(0, un);
+    __syncthreads();
+    int buf = 0;
+    for (int64_t rb = r0; rb < r1; rb += CY_CH, buf ^= 1) {
+        const int nr = (int)min((int64_t)CY_CH, r1 - rb);
+        load_u(rb + CY_CH, un);  // next chunk's U rows, stored after this chunk
+        if (gi < ng) {
+            const float4 *uc = Us + buf * CY_CH * UQ;
+            const int nmine = nr > gi ? (nr - gi + ng - 1) / ng : 0;  // rows gi, gi + ng, ... of the chunk
+            float4 cur[RB], nxt[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+                cur[u] = u < nmine ? __ldg(Y4 + (size_t)(rb + gi + u * ng) * tpr) : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int j0 = 0; j0 < nmine; j0 += RB) {
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    const int jn = j0 + RB + u;
+                    nxt[u] = jn < nmine ? __ldg(Y4 + (size_t)(rb + gi + jn * ng) * tpr) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    if (j0 + u >= nmine) break;
+                    const float4 *u4 = uc + (size_t)(gi + (j0 + u) * ng) * UQ;
+#pragma unroll
+                    for (int kq = 0; kq < UQ; ++kq) {
+                        const float4 uq = u4[kq];
+                        const float uu[4] = {uq.x, uq.y, uq.z, uq.w};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) {
+                            float4 &a = acc[4 * kq + c];
+                            a.x = fmaf(uu[c], cur[u].x, a.x);
+                            a.y = fmaf(uu[c], cur[u].y, a.y);
+                            a.z = fmaf(uu[c], cur[u].z, a.z);
+                            a.w = fmaf(uu[c], cur[u].w, a.w);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < RB; ++u) cur[u] = nxt[u];
             }
         }
+        store_u(buf ^ 1, un);
+        __syncthreads();
+    }
+    if (gi < ng) {
 #pragma unroll
-        for (int k = 0; k < KN; ++k) reinterpret_cast<float4 *>(red + (size_t)gi * KN * Pm + (size_t)k * Pm)[eq] = acc[k];
+        for (int k = 0; k < KN; ++k) reinterpret_cast<float4 *>(red + (size_t)gi * KnPm + (size_t)k * Pm)[eq] = acc[k];
     }
     __syncthreads();
-    const int KnPm = KN * Pm;
     for (int p = threadIdx.x; p < KnPm; p += blockDim.x) {
         float s = 0.f;
         for (int q = 0; q < ng; ++q) s += red[(size_t)q * KnPm + p];
@@ -1022,11 +1116,16 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
     HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * Kn * sizeof(float), c->stream));
     if (M.R > 0 && (Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && (size_t)Pm * Kn * 4 <= 96 * 1024) {
         const size_t sm2 = (size_t)Pm * Kn * sizeof(float);
-        const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, 256 * 4), (int64_t)c->num_sms * 4));
+        // one wave of CTAs with equal row ranges
 #define HQ_AY(KV)                                                                                             \
     if (Kn == KV) {                                                                                           \
         HQ_CUDA(cudaFuncSetAttribute(k_a_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
-        k_a_from_y2<KV><<<g2, 256, sm2, c->stream>>>(c->Y, Gn, M.row_id, M.R, Pm, A_out);                   \
+        int per_sm = 1;                                                                                       \
+        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_a_from_y2<KV>, 256, sm2));           \
+        const int g2 = (int)std::max<int64_t>(                                                                \
+            1, std::min<int64_t>(ceil_div(M.R, 2 * ay_rt<KV>()), (int64_t)c->num_sms * std::max(1, per_sm)));       \
+        const int64_t rpb2 = ceil_div(M.R, g2);                                                               \
+        k_a_from_y2<KV><<<g2, 256, sm2, c->stream>>>(c->Y, Gn, M.row_id, M.R, rpb2, Pm, A_out);             \
     }
         HQ_AY(4)
         HQ_AY(8)
@@ -1052,15 +1151,21 @@ hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
     const int Pm = (int)(c->P / Kn);
     const int Knp = (Kn + 3) & ~3;
     const int64_t R = M.R;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
-                                                                (int64_t)c->num_sms * 2));
-    const int64_t rpb = ceil_div(std::max<int64_t>(R, 1), grid);
+    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
+                                                          (int64_t)c->num_sms * 2));
+    int64_t rpb = ceil_div(std::max<int64_t>(R, 1), grid);
     if ((Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && Pm <= 1024 &&
-        (size_t)(256 / (Pm / 4)) * Kn * Pm * 4 <= 200 * 1024) {
-        const size_t sm2 = (size_t)(256 / (Pm / 4)) * Kn * Pm * sizeof(float);
+        (size_t)(256 / (Pm / 4)) * Kn * Pm * 4 + (size_t)2 * CY_CH * Kn * 4 <= 200 * 1024) {
+        const size_t sm2 = ((size_t)(256 / (Pm / 4)) * Kn * Pm + (size_t)2 * CY_CH * Kn) * sizeof(float);
+        // one wave: as many CTAs as are resident at once (at most 2 per SM)
 #define HQ_CY(KV)                                                                                                \
     if (Kn == KV) {                                                                                              \
         HQ_CUDA(cudaFuncSetAttribute(k_core_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
+        int per_sm = 1;                                                                                          \
+        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_core_from_y2<KV>, 256, sm2));           \
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),              \
+                                                           (int64_t)c->num_sms * std::min(2, std::max(1, per_sm)))); \
+        rpb = ceil_div(std::max<int64_t>(R, 1), grid);                                                           \
         k_core_from_y2<KV><<<grid, 256, sm2, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Pm, rpb,    \
                                                           (float *)c->core_part);                                \
     }

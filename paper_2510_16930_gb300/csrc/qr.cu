@@ -1,7 +1,9 @@
 // Orthonormalisation U_n <- orthonormal basis of A_n (Alg. 2, the QR step).
 //
-// CholeskyQR2 in FP64: W = A^T A (Gram, FP64 sums in a fixed order),
-// W = R^T R (Cholesky, one CTA), A <- A R^{-1}; then once more on the result.
+// CholeskyQR2 in FP64: W = A^T A (Gram, FP64 sums in a fixed order; for an
+// FP32 A double-float sums on the FP32 pipes, see k_gram_df), W = R^T R
+// (Cholesky in FP64, one CTA), A <- A R^{-1} (row-wise substitution); then
+// once more on the result.
 // Both R factors have a positive diagonal, so the result is the Q of the thin
 // QR with diag(R) > 0.  A_n = Y_(n) G_(n)^T with G_(n) = U_n^T Y_(n) squares
 // the conditioning of Y_(n), so a first pivot that is not clearly positive is
@@ -91,65 +93,273 @@ __global__ void __launch_bounds__(GRAM_TPB) k_gram_partial(const T *A, int64_t I
     }
 }
 
-// 1 / sqrt(d) in FP64 for 1e-30 < d < 1e30: the FP32 estimate refined by two
-// Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which doubles the number
-// of correct bits (about 22 -> 44 -> full FP64).  FP64 divisions and square
-// roots are long instruction sequences on this GPU; a pivot of the Cholesky
-// needs both, and the pivots are sequential.
-__device__ __forceinline__ double rsqrt_fp64(double d) {
-    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
-    y = y * (1.5 - 0.5 * d * y * y);
-    y = y * (1.5 - 0.5 * d * y * y);
-    return y;
+// ---- double-float arithmetic (a value is hi + lo, two FP32 numbers): the
+// Gram of an FP32 A on the FP32 pipes, which run 64 times as many
+// multiply-adds per clock as the FP64 pipe of this GPU.  Intrinsics with
+// explicit rounding keep the compiler from fusing the error terms away.
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2): a + b = s + e exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bv = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv));
 }
 
-// W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal):
-// thread per pair (coalesced across the threads for each block), eight
-// interleaved partial sums so eight loads are in flight, combined in a fixed
-// order (same result every run)
-__device__ void gram_sum(const double *part, int nblk, int K, double shift, double *W) {
-    const int npairs = K * (K + 1) / 2;
-    for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
-        double s8[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        int b = 0;
-        for (; b + 8 <= nblk; b += 8)
+// (hi, lo) += a b: the product split exactly by an FMA (TwoProduct), its high
+// part added to hi by TwoSum, both error terms to lo (the Dot2 step of Ogita,
+// Rump and Oishi, SIAM J. Sci. Comput. 26(6), 2005)
+__device__ __forceinline__ void df_fma(float a, float b, float &hi, float &lo) {
+    const float p = __fmul_rn(a, b);
+    const float e = __fmaf_rn(a, b, -p);
+    float s, q;
+    two_sum(hi, p, s, q);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(q, e));
+}
+
+// (hi, lo) += (bh, bl), renormalised so that lo is below half an ulp of hi
+__device__ __forceinline__ void df_add(float &hi, float &lo, float bh, float bl) {
+    float s, q;
+    two_sum(hi, bh, s, q);
+    q = __fadd_rn(q, __fadd_rn(lo, bl));
+    two_sum(s, q, hi, lo);
+}
+
+constexpr int DF_ROWS = 256;  // rows staged per step; each row stream's level-1 sum spans one step
+
+template <int KC, int TS>
+struct DfShape {
+    static constexpr int NTB = KC / TS;                // tile rows and columns
+    static constexpr int NT = NTB * (NTB + 1) / 2;     // tiles on and above the diagonal
+    static constexpr int S = GRAM_TPB / NT;            // row streams per tile
+    static constexpr int NP = KC * (KC + 1) / 2;       // Gram entries i <= j
+    static constexpr int TILE_B = DF_ROWS * KC * 4;
+    static constexpr int RED_B = S * NT * TS * TS * 8;
+    static constexpr int SMEM_B = TILE_B > RED_B ? TILE_B : RED_B;
+};
+
+// Gram partials W(i, j) = sum over the CTA's rows of A(r, i) A(r, j), i <= j,
+// for an FP32 A with KC in {4, 8, 16, 32} columns (16-byte aligned rows), in
+// double-float: thread = (TS x TS tile of W on or above the diagonal, row
+// stream); a stream's products over one staged step of DF_ROWS rows are summed
+// in a level-1 pair (Dot2), which is then added to a level-2 pair, so no
+// running sum spans more than about 40 products; the streams are added in
+// stream order at the end.  part: [block][pair] as (hi, lo).
+template <int KC, int TS>
+__global__ void __launch_bounds__(GRAM_TPB) k_gram_df(const float *A, int64_t I, int64_t rows_per_block,
+                                                      float2 *part, const int32_t *flag, int pass) {
+    using D = DfShape<KC, TS>;
+    if (qr_skip(flag, pass)) return;
+    __shared__ __align__(16) unsigned char smem[D::SMEM_B];
+    float *tile = reinterpret_cast<float *>(smem);
+    const int t = threadIdx.x, tid = t % D::NT, st = t / D::NT;
+    const bool active = st < D::S;
+    int ti = 0, rem = tid;
+    while (rem >= D::NTB - ti) {
+        rem -= D::NTB - ti;
+        ++ti;
+    }
+    const int tj = ti + rem;
+    float h2[TS][TS], l2[TS][TS];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) s8[u] += part[(size_t)(b + u) * npairs + p];
-        for (int u = 0; b < nblk; ++b, ++u) s8[u] += part[(size_t)b * npairs + p];
-        const double s = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
-        int rem = p, i = 0;
-        while (rem >= K - i) {
-            rem -= K - i;
+    for (int u = 0; u < TS; ++u)
+#pragma unroll
+        for (int v = 0; v < TS; ++v) h2[u][v] = l2[u][v] = 0.f;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
+    const int64_t r1 = min(r0 + rows_per_block, I);
+    for (int64_t rb = r0; rb < r1; rb += DF_ROWS) {
+        const int nr = (int)min((int64_t)DF_ROWS, r1 - rb);
+        __syncthreads();
+        const float4 *src = reinterpret_cast<const float4 *>(A + rb * KC);
+        for (int q = t; q < nr * (KC / 4); q += GRAM_TPB) reinterpret_cast<float4 *>(tile)[q] = __ldg(src + q);
+        __syncthreads();
+        if (active) {
+            float h1[TS][TS], l1[TS][TS];
+#pragma unroll
+            for (int u = 0; u < TS; ++u)
+#pragma unroll
+                for (int v = 0; v < TS; ++v) h1[u][v] = l1[u][v] = 0.f;
+            for (int r = st; r < nr; r += D::S) {
+                float a[TS], b[TS];
+                if constexpr (TS == 2) {
+                    const float2 x = *reinterpret_cast<const float2 *>(tile + r * KC + ti * TS);
+                    const float2 y = *reinterpret_cast<const float2 *>(tile + r * KC + tj * TS);
+                    a[0] = x.x, a[1] = x.y, b[0] = y.x, b[1] = y.y;
+                } else {
+                    const float4 x = *reinterpret_cast<const float4 *>(tile + r * KC + ti * TS);
+                    const float4 y = *reinterpret_cast<const float4 *>(tile + r * KC + tj * TS);
+                    a[0] = x.x, a[1] = x.y, a[2] = x.z, a[3] = x.w;
+                    b[0] = y.x, b[1] = y.y, b[2] = y.z, b[3] = y.w;
+                }
+#pragma unroll
+                for (int u = 0; u < TS; ++u)
+#pragma unroll
+                    for (int v = 0; v < TS; ++v) df_fma(a[u], b[v], h1[u][v], l1[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < TS; ++u)
+#pragma unroll
+                for (int v = 0; v < TS; ++v) df_add(h2[u][v], l2[u][v], h1[u][v], l1[u][v]);
+        }
+    }
+    __syncthreads();
+    float2 *red = reinterpret_cast<float2 *>(smem);  // [S][NT][TS][TS]
+    if (active)
+#pragma unroll
+        for (int u = 0; u < TS; ++u)
+#pragma unroll
+            for (int v = 0; v < TS; ++v) red[(st * D::NT + tid) * TS * TS + u * TS + v] = make_float2(h2[u][v], l2[u][v]);
+    __syncthreads();
+    for (int p = t; p < D::NP; p += GRAM_TPB) {
+        int i = 0, rm = p;
+        while (rm >= KC - i) {
+            rm -= KC - i;
             ++i;
         }
-        W[i * K + i + rem] = rem == 0 ? s + shift : s;
+        const int j = i + rm;
+        const int a = i / TS, b = j / TS;  // a <= b
+        const int tile_idx = a * D::NTB - a * (a - 1) / 2 + (b - a);
+        const int e = (tile_idx * TS + i % TS) * TS + j % TS;
+        float hi = 0.f, lo = 0.f;
+        for (int q = 0; q < D::S; ++q) {
+            const float2 x = red[q * D::NT * TS * TS + e];
+            df_add(hi, lo, x.x, x.y);
+        }
+        part[(size_t)blockIdx.x * D::NP + p] = make_float2(hi, lo);
+    }
+}
+
+constexpr int CHOL_TPB = 1024;
+
+// Sum of the partials b0 <= b < b1 of pair p: four interleaved sums, combined
+// in a fixed order.  DF: double-float partials summed in double-float.
+template <bool DF>
+struct PartSum {
+    float hi = 0.f, lo = 0.f;
+    double d = 0.0;
+};
+
+template <bool DF>
+__device__ PartSum<DF> sum_range(const void *part_v, int npairs, int p, int b0, int b1) {
+    PartSum<DF> r;
+    if constexpr (DF) {
+        const float2 *part = static_cast<const float2 *>(part_v);
+        float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
+        int b = b0;
+        for (; b + 4 <= b1; b += 4) {
+            float2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) x[u] = part[(size_t)(b + u) * npairs + p];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) df_add(h4[u], l4[u], x[u].x, x[u].y);
+        }
+        for (int u = 0; b < b1; ++b, ++u) {
+            const float2 x = part[(size_t)b * npairs + p];
+            df_add(h4[u], l4[u], x.x, x.y);
+        }
+        df_add(h4[0], l4[0], h4[1], l4[1]);
+        df_add(h4[2], l4[2], h4[3], l4[3]);
+        df_add(h4[0], l4[0], h4[2], l4[2]);
+        r.hi = h4[0];
+        r.lo = l4[0];
+    } else {
+        const double *part = static_cast<const double *>(part_v);
+        double s4[4] = {0, 0, 0, 0};
+        int b = b0;
+        for (; b + 4 <= b1; b += 4)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s4[u] += part[(size_t)(b + u) * npairs + p];
+        for (int u = 0; b < b1; ++b, ++u) s4[u] += part[(size_t)b * npairs + p];
+        r.d = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    }
+    return r;
+}
+
+__device__ __forceinline__ void put_pair(double *W, int K, int p, double s, double shift) {
+    int rem = p, i = 0;
+    while (rem >= K - i) {
+        rem -= K - i;
+        ++i;
+    }
+    W[i * K + i + rem] = rem == 0 ? s + shift : s;
+}
+
+// W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal).
+// When the pairs are fewer than the threads, the nblk partials of each pair
+// are split into nsub = blockDim / npairs contiguous block ranges, one thread
+// per (pair, range), and the nsub sums of a pair are added in range order
+// afterwards; otherwise a thread sums all partials of its pairs.  Either way
+// the order is fixed (same result every run).  DF sums are rounded to FP64
+// once, at the end.  sub: shared scratch of blockDim doubles.
+template <bool DF>
+__device__ void gram_sum(const void *part_v, int nblk, int K, double shift, double *W, double *sub) {
+    const int npairs = K * (K + 1) / 2;
+    const int nsub = (int)blockDim.x / npairs;
+    const int t = threadIdx.x;
+    if (nsub <= 1) {
+        for (int p = t; p < npairs; p += blockDim.x) {
+            const PartSum<DF> r = sum_range<DF>(part_v, npairs, p, 0, nblk);
+            put_pair(W, K, p, DF ? (double)r.hi + (double)r.lo : r.d, shift);
+        }
+        return;
+    }
+    if (t < nsub * npairs) {
+        const int p = t % npairs, q = t / npairs;
+        const int b0 = (int)((int64_t)nblk * q / nsub), b1 = (int)((int64_t)nblk * (q + 1) / nsub);
+        const PartSum<DF> r = sum_range<DF>(part_v, npairs, p, b0, b1);
+        if constexpr (DF)
+            reinterpret_cast<float2 *>(sub)[t] = make_float2(r.hi, r.lo);
+        else
+            sub[t] = r.d;
+    }
+    __syncthreads();
+    for (int p = t; p < npairs; p += blockDim.x) {
+        double s = 0.0;
+        if constexpr (DF) {
+            const float2 *sb = reinterpret_cast<const float2 *>(sub);
+            float hi = 0.f, lo = 0.f;
+            for (int q = 0; q < nsub; ++q) df_add(hi, lo, sb[q * npairs + p].x, sb[q * npairs + p].y);
+            s = (double)hi + (double)lo;
+        } else {
+            for (int q = 0; q < nsub; ++q) s += sub[q * npairs + p];
+        }
+        put_pair(W, K, p, s, shift);
     }
 }
 
 // W = R^T R in place (R in the upper triangle), inv(j) = 1 / R(j, j); one warp,
-// lane k holds column k, so the sequential pivots need no block barrier.
-// Returns 1 when a pivot is not above 1e-14 max_j W(j, j).
-__device__ int chol_warp(double *W, double *inv, int K, int lane) {
+// right-looking: step j scales row j by 1 / sqrt(pivot) and subtracts its
+// outer product from the trailing triangle, whose entries the lanes share
+// (pairs[] lists the upper triangle by row k from K-1 down, so the trailing
+// triangle of step j is its first (K-j-1)(K-j)/2 entries, packed k * 64 + l).
+// 1 / sqrt(pivot) for 1e-30 < pivot < 1e30 is the FP32 estimate refined by NR
+// Newton-Raphson steps y <- y (3 - d y^2) / 2, each of which doubles the
+// number of correct bits (about 22 -> 44 -> full FP64): FP64 divisions and
+// square roots are long instruction sequences on this GPU, and the pivots are
+// sequential.  Returns 1 when a pivot is not above tiny_rel max_j W(j, j).
+template <int NR>
+__device__ int chol_warp(double *W, double *inv, const uint16_t *pairs, int K, int lane, double tiny_rel) {
     double dmax = 0.0;
     for (int i = 0; i < K; ++i) dmax = fmax(dmax, W[i * K + i]);
-    const double tiny = 1e-14 * dmax;
+    const double tiny = tiny_rel * dmax;
     if (!(dmax > 0.0)) return 1;
     for (int j = 0; j < K; ++j) {
-        // pivot: d = W(j,j) - sum_{i<j} R(i,j)^2, a lane-strided sum in fixed order
-        double d = 0.0;
-        for (int i = lane; i < j; i += 32) d += W[i * K + j] * W[i * K + j];
-        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-        d = W[j * K + j] - d;
+        const double d = W[j * K + j];
         if (!(d > tiny)) return 1;
-        const double y = rsqrt_fp64(d);  // 1 / R(j, j)
-        // row j of R: R(j,k) = (W(j,k) - sum_{i<j} R(i,j) R(i,k)) / R(j,j), lane per k
-        for (int k = j + 1 + lane; k < K; k += 32) {
-            double s = W[j * K + k];
-            for (int i = 0; i < j; ++i) s -= W[i * K + j] * W[i * K + k];
-            W[j * K + k] = s * y;
+        double y;
+        if (d > 1e-30 && d < 1e30) {
+            y = (double)rsqrtf((float)d);
+#pragma unroll
+            for (int it = 0; it < NR; ++it) y = y * (1.5 - 0.5 * d * y * y);
+        } else {
+            y = 1.0 / sqrt(d);
         }
+        for (int k = j + 1 + lane; k < K; k += 32) W[j * K + k] *= y;
         __syncwarp();
+        const int nt = (K - j - 1) * (K - j) / 2;
+        for (int q = lane; q < nt; q += 32) {
+            const int k = pairs[q] >> 6, l = pairs[q] & 63;
+            W[k * K + l] = fma(-W[j * K + k], W[j * K + l], W[k * K + l]);
+        }
         if (lane == 0) {
             W[j * K + j] = d * y;
             inv[j] = y;
@@ -160,22 +370,43 @@ __device__ int chol_warp(double *W, double *inv, int K, int lane) {
 }
 
 // Sum of the Gram partials, Cholesky W = R^T R (of W + s I after a breakdown in
-// the first pass), Rinv = R^{-1}.  The partial sums use all warps; the
-// factorisation and the inverse run in warp 0.  m = rows of A.
-__global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int K, int64_t m, double *Rinv,
-                                              int32_t *flag, int pass) {
+// the first pass).  Rd receives R with 1 / R(j, j) on its diagonal and zeros
+// below it, the form the row substitution of the apply step reads.  The
+// partial sums use all threads; the factorisation runs in warp 0.  m = rows
+// of A.  A pivot counts as not clearly positive below 1e-14 of the largest
+// diagonal entry for FP64 sums and below 1e-13 for double-float ones (whose
+// rounding error is up to ten times larger).  The double-float (FP32 data)
+// form refines the reciprocal square root by one Newton-Raphson step (about
+// 2e-14 relative: the factor is stored in FP32), the FP64 form by two.
+template <bool DF>
+__global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, int K, int64_t m, double *Rd,
+                                                   int32_t *flag, int pass) {
     if (qr_skip(flag, pass)) return;
     __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
     __shared__ double inv[HOQRI_MAXK];  // 1 / R(j, j)
+    __shared__ double sub[CHOL_TPB];
+    __shared__ uint16_t pairs[HOQRI_MAXK * (HOQRI_MAXK + 1) / 2];
     __shared__ int s_bad;
     __shared__ double s_shift;
+    constexpr double tiny_rel = DF ? 1e-13 : 1e-14;
+    constexpr int NR = DF ? 1 : 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    gram_sum(part, nblk, K, 0.0, W);
+    const int npairs = K * (K + 1) / 2;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        // entry q of the list: rows k = K-1, K-2, ... with K - k entries each
+        int k = K - 1, rem = q;
+        while (rem >= K - k) {
+            rem -= K - k;
+            --k;
+        }
+        pairs[q] = (uint16_t)(k * 64 + k + rem);
+    }
+    gram_sum<DF>(part, nblk, K, 0.0, W, sub);
     __syncthreads();
     if (wid == 0) {
         double tr = 0.0;
         for (int i = 0; i < K; ++i) tr += W[i * K + i];
-        const int bad = chol_warp(W, inv, K, lane);
+        const int bad = chol_warp<NR>(W, inv, pairs, K, lane, tiny_rel);
         if (lane == 0) {
             s_bad = bad;
             s_shift = 11.0 * ((double)m * K + (double)K * (K + 1)) * 0x1p-53 * tr;
@@ -183,10 +414,10 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
     }
     __syncthreads();
     if (s_bad && pass == 0 && s_shift > 0.0) {
-        gram_sum(part, nblk, K, s_shift, W);
+        gram_sum<DF>(part, nblk, K, s_shift, W, sub);
         __syncthreads();
         if (wid == 0) {
-            const int bad = chol_warp(W, inv, K, lane);
+            const int bad = chol_warp<NR>(W, inv, pairs, K, lane, tiny_rel);
             if (lane == 0) {
                 s_bad = bad;
                 if (!bad) flag[3] = 1;
@@ -202,36 +433,26 @@ __global__ void __launch_bounds__(256) k_chol(const double *part, int nblk, int 
         }
         return;
     }
-    // Rinv: lane col solves R x = e_col by back substitution (x upper triangular);
-    // x(i) for i < col is kept in the free strictly-lower entry W(col, i)
-    for (int col = lane; col < K; col += 32) {
-        const double xd = inv[col];
-        for (int i = col - 1; i >= 0; --i) {
-            double s = -W[i * K + col] * xd;
-            for (int k = i + 1; k < col; ++k) s -= W[i * K + k] * W[col * K + k];
-            W[col * K + i] = s * inv[i];
-        }
-        Rinv[col * K + col] = xd;
-    }
-    __syncwarp();
     for (int t = lane; t < K * K; t += 32) {
         const int i = t / K, col = t - i * K;
-        if (i != col) Rinv[t] = i > col ? 0.0 : W[col * K + i];
+        Rd[t] = i > col ? 0.0 : (i == col ? inv[i] : W[t]);
     }
 }
 
-// out(r, :) = A(r, :) Rinv (Rinv upper triangular), one thread per row; the
-// thread reads its whole row before writing, so out may alias A.  FP32 rows
-// are multiplied in FP32 (the factor is stored in FP32), FP64 rows in FP64.
+// out(r, :) = A(r, :) R^{-1}: each row solves x R = a by forward substitution,
+// x(c) = (a(c) - sum_{i<c} x(i) R(i, c)) / R(c, c), with Rd as k_chol writes it
+// (1 / R(c, c) on the diagonal); one thread per row, which reads its whole row
+// before writing, so out may alias A.  FP32 rows are solved in FP32 (the
+// factor is stored in FP32), FP64 rows in FP64.
 template <typename T, int KC>
-__global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const double *Rinv, T *out,
+__global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const double *Rd, T *out,
                                                     const int32_t *flag, int pass) {
     if (qr_skip(flag, pass)) return;
     __shared__ T Rs[KC * KC];
-    for (int t = threadIdx.x; t < KC * KC; t += blockDim.x) Rs[t] = (T)Rinv[t];
+    for (int t = threadIdx.x; t < KC * KC; t += blockDim.x) Rs[t] = (T)Rd[t];
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
-        T a[KC], o[KC];
+        T a[KC];
         if constexpr (sizeof(T) == 4 && KC % 4 == 0) {
             // a row is KC/4 aligned 16-byte vectors
 #pragma unroll
@@ -248,57 +469,56 @@ __global__ void __launch_bounds__(256) k_apply_rows(const T *A, int64_t I, const
         }
 #pragma unroll
         for (int c = 0; c < KC; ++c) {
-            T s = T(0);
+            a[c] *= Rs[c * KC + c];
 #pragma unroll
-            for (int i = 0; i <= c; ++i) s = fma(a[i], Rs[i * KC + c], s);
-            o[c] = s;
+            for (int k = c + 1; k < KC; ++k) a[k] = fma(-a[c], Rs[c * KC + k], a[k]);
         }
         if constexpr (sizeof(T) == 4 && KC % 4 == 0) {
 #pragma unroll
             for (int i = 0; i < KC / 4; ++i)
                 reinterpret_cast<float4 *>(out + r * KC)[i] =
-                    make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+                    make_float4(a[4 * i], a[4 * i + 1], a[4 * i + 2], a[4 * i + 3]);
         } else {
 #pragma unroll
-            for (int c = 0; c < KC; ++c) out[r * KC + c] = o[c];
+            for (int c = 0; c < KC; ++c) out[r * KC + c] = a[c];
         }
     }
 }
 
-// any K <= 64: one thread per row, row kept in local memory
+// any K <= 64: one thread per row, row kept in local memory, solved in FP64
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, int K, const double *Rinv, T *out,
+__global__ void __launch_bounds__(256) k_apply_rows_any(const T *A, int64_t I, int K, const double *Rd, T *out,
                                                         const int32_t *flag, int pass) {
     if (qr_skip(flag, pass)) return;
     __shared__ double Rs[HOQRI_MAXK * HOQRI_MAXK];
-    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rinv[t];
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) Rs[t] = Rd[t];
     __syncthreads();
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < I; r += (int64_t)gridDim.x * blockDim.x) {
         double a[HOQRI_MAXK];
         for (int i = 0; i < K; ++i) a[i] = (double)A[r * K + i];
         for (int c = 0; c < K; ++c) {
-            double s = 0.0;
-            for (int i = 0; i <= c; ++i) s += a[i] * Rs[i * K + c];
-            out[r * K + c] = (T)s;
+            a[c] *= Rs[c * K + c];
+            for (int k = c + 1; k < K; ++k) a[k] = fma(-a[c], Rs[c * K + k], a[k]);
+            out[r * K + c] = (T)a[c];
         }
     }
 }
 
 template <typename T>
-void launch_apply(cudaStream_t st, const int32_t *flag, int pass, const T *A, int64_t I, int K, const double *Rinv,
+void launch_apply(cudaStream_t st, const int32_t *flag, int pass, const T *A, int64_t I, int K, const double *Rd,
                   T *out, int grid) {
     // the fixed-width kernels move FP32 rows as 16-byte vectors: both buffers must be 16-byte aligned
     const bool aligned = ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(out)) & 15) == 0;
     if (!aligned) {
-        k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag, pass);
+        k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rd, out, flag, pass);
         return;
     }
     switch (K) {
-        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
-        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
-        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
-        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rinv, out, flag, pass); break;
-        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rinv, out, flag, pass); break;
+        case 4: k_apply_rows<T, 4><<<grid, 256, 0, st>>>(A, I, Rd, out, flag, pass); break;
+        case 8: k_apply_rows<T, 8><<<grid, 256, 0, st>>>(A, I, Rd, out, flag, pass); break;
+        case 16: k_apply_rows<T, 16><<<grid, 256, 0, st>>>(A, I, Rd, out, flag, pass); break;
+        case 32: k_apply_rows<T, 32><<<grid, 256, 0, st>>>(A, I, Rd, out, flag, pass); break;
+        default: k_apply_rows_any<T><<<grid, 256, 0, st>>>(A, I, K, Rd, out, flag, pass); break;
     }
 }
 
@@ -418,6 +638,30 @@ __global__ void k_gauss(T *out, int64_t n, uint64_t seed, uint32_t stream_id) {
     }
 }
 
+// Gram partials and Cholesky of one pass: in double-float for an FP32 A with K
+// in {4, 8, 16, 32} and 16-byte aligned rows, in FP64 otherwise.
+template <typename T>
+void launch_gram_chol(cudaStream_t st, const T *src, int64_t I, int K, int nb, int64_t rpb, void *part, double *Rd,
+                      int32_t *flag, int pass) {
+    bool df = false;
+    if constexpr (sizeof(T) == 4) {
+        df = (K == 4 || K == 8 || K == 16 || K == 32) && (reinterpret_cast<uintptr_t>(src) & 15) == 0;
+        float2 *p2 = static_cast<float2 *>(part);
+        if (df) switch (K) {
+                case 4: k_gram_df<4, 2><<<nb, GRAM_TPB, 0, st>>>(src, I, rpb, p2, flag, pass); break;
+                case 8: k_gram_df<8, 2><<<nb, GRAM_TPB, 0, st>>>(src, I, rpb, p2, flag, pass); break;
+                case 16: k_gram_df<16, 2><<<nb, GRAM_TPB, 0, st>>>(src, I, rpb, p2, flag, pass); break;
+                default: k_gram_df<32, 4><<<nb, GRAM_TPB, 0, st>>>(src, I, rpb, p2, flag, pass); break;
+            }
+    }
+    if (df) {
+        k_chol<true><<<1, CHOL_TPB, 0, st>>>(part, nb, K, I, Rd, flag, pass);
+    } else {
+        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, static_cast<double *>(part), flag, pass);
+        k_chol<false><<<1, CHOL_TPB, 0, st>>>(part, nb, K, I, Rd, flag, pass);
+    }
+}
+
 __global__ void k_set_flag(int32_t *flag, int32_t v) {
     flag[0] = v;
     flag[3] = 0;
@@ -438,7 +682,7 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     const int nb = gram_blocks(I, c->num_sms);
     const int64_t rpb = ceil_div(I, nb);
     const int npairs = K * (K + 1) / 2;
-    double *Rinv = c->qr_small;
+    double *Rd = c->qr_small;
     const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
     // flag 0: CholeskyQR2; flag 1 (qr_kind 1): Householder from the start; no
     // shift yet.  Set with a kernel, not a copy from host memory, so a captured
@@ -448,10 +692,9 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     // pass 0: A <- A R1^{-1}; pass 1: U = A R2^{-1}; pass 2 (after a shift): U <- U R3^{-1}
     for (int pass = 0; pass < QR_PASSES; ++pass) {
         T *src = pass < 2 ? A : U;
-        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, c->qr_part, c->dflag, pass);
-        k_chol<<<1, 256, 0, st>>>(c->qr_part, nb, K, I, Rinv, c->dflag, pass);
+        launch_gram_chol<T>(st, src, I, K, nb, rpb, c->qr_part, Rd, c->dflag, pass);
         k_householder<T><<<1, HH_TPB, 0, st>>>(src, I, K, c->qr_work, c->qr_work + I * K, U, c->dflag);
-        launch_apply<T>(st, c->dflag, pass, src, I, K, Rinv, pass == 0 ? A : U, apply_rows_grid);
+        launch_apply<T>(st, c->dflag, pass, src, I, K, Rd, pass == 0 ? A : U, apply_rows_grid);
         c->nlaunch += 4;
     }
     (void)npairs;
@@ -498,7 +741,7 @@ hoqri_status init_factors_seeded(hoqri_ctx *c) {
 // ---- allocation-free CholeskyQR2 (hoqri_orthonormalize_noalloc): the same
 // Gram / Cholesky / apply kernels (shifted first pass included), with their
 // scratch in one file-scope device array instead of context buffers.  Layout:
-// Gram partials of up to NA_BLOCKS blocks | R^{-1} | flag[4] (on a 256-byte
+// Gram partials of up to NA_BLOCKS blocks | R (diagonal 1 / R(j, j)) | flag[4] (on a 256-byte
 // boundary).
 namespace {
 
@@ -546,7 +789,7 @@ hoqri_status orthonormalize_noalloc_t(int64_t I, int K, const T *A, T *U, cudaSt
     int sms = 1;
     HQ_TRY(na_scratch(&base, &sms));
     double *part = reinterpret_cast<double *>(base);
-    double *Rinv = reinterpret_cast<double *>(base + NA_PART_BYTES);
+    double *Rd = reinterpret_cast<double *>(base + NA_PART_BYTES);
     int32_t *flag = reinterpret_cast<int32_t *>(base + NA_PART_BYTES + NA_RINV_BYTES);
     const int nb = std::min(gram_blocks(I, sms), NA_BLOCKS);
     const int64_t rpb = ceil_div(I, nb);
@@ -556,9 +799,8 @@ hoqri_status orthonormalize_noalloc_t(int64_t I, int K, const T *A, T *U, cudaSt
     // pass only): U = U R^{-1} in place, row by row
     for (int pass = 0; pass < QR_PASSES; ++pass) {
         const T *src = pass == 0 ? A : U;
-        k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, part, flag, pass);
-        k_chol<<<1, 256, 0, st>>>(part, nb, K, I, Rinv, flag, pass);
-        launch_apply<T>(st, flag, pass, src, I, K, Rinv, U, grid);
+        launch_gram_chol<T>(st, src, I, K, nb, rpb, part, Rd, flag, pass);
+        launch_apply<T>(st, flag, pass, src, I, K, Rd, U, grid);
     }
     HQ_CUDA(cudaGetLastError());
     int32_t f = 0;
