@@ -86,7 +86,8 @@ typedef struct {
                            the core G = U_n^T Y_(n); 2: the paper's O(IK) memory form
                            (separate core pass, no Y) */
     uint64_t seed;      /* seed of the initial factors when U0 is NULL */
-    double tol;         /* hoqri_run: stop when |r_t - r_{t-1}| < tol (0: never) */
+    double tol;         /* hoqri_run: stop after the first sweep whose residual differs
+                           from the previous one by less than tol (0: never) */
 } hoqri_options;
 
 /* Fills *opt with the defaults (FP32, CholeskyQR2 + fallback, library-chosen
@@ -139,6 +140,32 @@ HOQRI_API hoqri_status hoqri_orthonormalize(hoqri_ctx *ctx, int32_t mode, const 
  * which equals ||X - G x {U}|| / ||X|| for orthonormal U and optimal G (Sec. 2.2).
  */
 HOQRI_API hoqri_status hoqri_iterate(hoqri_ctx *ctx, int32_t iters, double *resid_hist);
+
+/*
+ * Runs sweeps of Alg. 2 as hoqri_iterate does, at most max_iters of them, and
+ * stops after the first sweep t whose residual satisfies |r_t - r_{t-1}| < tol
+ * (options.tol; r_0 is the residual of the core before the first sweep): the
+ * stopping rule of Sec. 6.1.  With tol = 0 every sweep runs.  Each sweep then
+ * ends with a device-to-host read of its residual (the stream is synchronised
+ * once per sweep).  resid_hist (host, NULL or max_iters doubles) receives
+ * r_1 .. r_done; iters_done (host, NULL allowed) the number of sweeps run.  The
+ * results of the sweeps that ran are identical to those of hoqri_iterate with
+ * that count.  Errors: HOQRI_ERR_INVALID for max_iters < 0 or tol < 0, else as
+ * hoqri_iterate.
+ */
+HOQRI_API hoqri_status hoqri_run(hoqri_ctx *ctx, int32_t max_iters, double *resid_hist, int32_t *iters_done);
+
+/*
+ * ||grad f||^2 at the current factors, f = ||X x {U^T}||^2 on the product of
+ * Stiefel manifolds (Sec. 5, Eq. tucker_grad and Eq. grad2):
+ * sum_n ||2 A_n - 2 U_n G_(n) G_(n)^T||_F^2 with A_n = TTMcTC(X, {U}, n) and G
+ * the core of the current factors; zero exactly at a stationary point
+ * (Def. stationary).  Each mode's term is formed row by row and summed in FP64
+ * in a fixed order.  Costs one core pass and one TTMcTC pass per mode; the
+ * factors are not changed (the context's core is left at that of the last
+ * mode).  out: host double.  Errors: HOQRI_ERR_INVALID for a NULL out.
+ */
+HOQRI_API hoqri_status hoqri_grad_norm2(hoqri_ctx *ctx, double *out);
 
 /* Copies the current factor U_mode (I_mode x K_mode reals) to U_out. */
 HOQRI_API hoqri_status hoqri_get_factor(hoqri_ctx *ctx, int32_t mode, void *U_out);

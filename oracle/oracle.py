@@ -186,6 +186,21 @@ def ttmctc_matrix(dims, idx, vals, U, n):
     return A
 
 
+def grad(dims, idx, vals, U, n):
+    """Block n of the Riemannian gradient of f = ||X x {U^T}||^2 on the product of
+    Stiefel manifolds at {U} (Sec. 5, Eq. tucker_grad): 2 A_n - 2 U_n G_(n) G_(n)^T,
+    A_n by Alg. 3 and G = X x {U^T}; G_(n) is the mode-n unfolding of the core
+    (the other modes ascending, the last fastest)."""
+    A, G = ttmctc(dims, idx, vals, U, n, return_core=True)
+    Gn = np.moveaxis(G, n, 0).reshape(G.shape[n], -1)
+    return 2.0 * A - 2.0 * (np.asarray(U[n], dtype=np.float64) @ (Gn @ Gn.T))
+
+
+def grad_norm2(dims, idx, vals, U):
+    """||grad f||^2 = sum over n of ||grad block n||_F^2 (Eq. grad2, first line)."""
+    return float(sum(np.sum(grad(dims, idx, vals, U, n) ** 2) for n in range(len(U))))
+
+
 def qr(A):
     """Householder thin QR with diag(R) >= 0: returns (Q, R, zero_pivots)."""
     A = np.ascontiguousarray(A, dtype=np.float64)

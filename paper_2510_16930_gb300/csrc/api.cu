@@ -577,13 +577,15 @@ static hoqri_status capture_sweep(hoqri_ctx *c) {
 
 }  // namespace hoqri
 
-hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
-    g_last_error.clear();
-    HQ_TRY(check_mode(c, 0));
-    if (iters < 0) {
-        set_error("hoqri_iterate: iters < 0");
-        return HOQRI_ERR_INVALID;
-    }
+namespace hoqri {
+
+// Up to `iters` sweeps of Alg. 2; with tol > 0 the sweeps stop after the first
+// one whose residual differs from the previous residual by less than tol (the
+// stopping rule of Sec. 6.1; the residual before the first sweep is that of
+// the initial core), which costs one device-to-host read per sweep.
+// *done receives the number of sweeps run.
+static hoqri_status run_sweeps(hoqri_ctx *c, int32_t iters, double tol, double *resid_hist, int32_t *done,
+                               const char *who) {
     const int N = c->N;
     HQ_TRY(ensure_slots(c, 2 + (int64_t)iters * N + 1));
     int32_t before = 0;
@@ -593,34 +595,112 @@ hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
     }
     // slot 2 + k holds ||G||^2 after k block updates (k = 0: the initial core)
     HQ_TRY(refresh_core(c, 0, c->dnorm + 2));
+    double h0[3] = {0, 0, 0};
+    if (tol > 0.0) {
+        HQ_CUDA(cudaMemcpyAsync(h0, c->dnorm, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        HQ_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    double r_prev = resid_of(h0[0], h0[2]);
     // sweeps replay one captured CUDA graph, unless tracing is on (its events
     // are recorded per call on the host side) or capture is unavailable
     const bool graphs = c->opt.use_graphs && !c->profiling && iters > 0 && !c->sweep_graph_off;
     if (graphs && !c->sweep_exec) HQ_TRY(capture_sweep(c));
-    if (graphs && c->sweep_exec) {
-        HQ_CUDA(cudaMemsetAsync(c->gcount, 0, sizeof(int32_t), c->stream));
-        for (int t = 0; t < iters; ++t) {
+    const bool replay = graphs && c->sweep_exec;
+    if (replay) HQ_CUDA(cudaMemsetAsync(c->gcount, 0, sizeof(int32_t), c->stream));
+    int32_t ran = 0;
+    for (int t = 0; t < iters; ++t) {
+        if (replay) {
             HQ_CUDA(cudaGraphLaunch(c->sweep_exec, c->stream));
             c->nlaunch += c->sweep_launches;
+        } else {
+            HQ_TRY(sweep(c, c->dnorm + 2 + (int64_t)t * N + 1));
         }
-    } else {
-        for (int t = 0; t < iters; ++t) HQ_TRY(sweep(c, c->dnorm + 2 + (int64_t)t * N + 1));
+        ++ran;
+        if (tol > 0.0) {
+            double g2 = 0.0;
+            HQ_CUDA(cudaMemcpyAsync(&g2, c->dnorm + 2 + (size_t)(t + 1) * N, sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+            HQ_CUDA(cudaStreamSynchronize(c->stream));
+            HQ_TRY(check_device_error(c));
+            const double r = resid_of(h0[0], g2);
+            if (std::fabs(r - r_prev) < tol) break;
+            r_prev = r;
+        }
     }
+    if (done) *done = ran;
     if (resid_hist || c->opt.qr_kind == 2) {
-        std::vector<double> h(2 + (size_t)iters * N + 1);
+        std::vector<double> h(2 + (size_t)ran * N + 1);
         HQ_CUDA(cudaMemcpyAsync(h.data(), c->dnorm, h.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         int32_t after = 0;
         HQ_CUDA(cudaMemcpyAsync(&after, c->dflag + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
         HQ_CUDA(cudaStreamSynchronize(c->stream));
         HQ_TRY(check_device_error(c));
         if (resid_hist)
-            for (int t = 0; t < iters; ++t) resid_hist[t] = resid_of(h[0], h[2 + (size_t)(t + 1) * N]);
+            for (int t = 0; t < ran; ++t) resid_hist[t] = resid_of(h[0], h[2 + (size_t)(t + 1) * N]);
         if (c->opt.qr_kind == 2 && after != before) {
-            set_error("hoqri_iterate: Cholesky breakdown in a QR step");
+            set_error(std::string(who) + ": Cholesky breakdown in a QR step");
             return HOQRI_ERR_QR_BREAKDOWN;
         }
     }
     HQ_CUDA(cudaGetLastError());
+    return HOQRI_OK;
+}
+
+}  // namespace hoqri
+
+hoqri_status hoqri_iterate(hoqri_ctx *c, int32_t iters, double *resid_hist) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (iters < 0) {
+        set_error("hoqri_iterate: iters < 0");
+        return HOQRI_ERR_INVALID;
+    }
+    return run_sweeps(c, iters, 0.0, resid_hist, nullptr, "hoqri_iterate");
+}
+
+hoqri_status hoqri_run(hoqri_ctx *c, int32_t max_iters, double *resid_hist, int32_t *iters_done) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (max_iters < 0 || !(c->opt.tol >= 0.0)) {
+        set_error("hoqri_run: max_iters < 0 or tol < 0");
+        return HOQRI_ERR_INVALID;
+    }
+    return run_sweeps(c, max_iters, c->opt.tol, resid_hist, iters_done, "hoqri_run");
+}
+
+hoqri_status hoqri_grad_norm2(hoqri_ctx *c, double *out) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (!out) {
+        set_error("hoqri_grad_norm2: out is NULL");
+        return HOQRI_ERR_INVALID;
+    }
+    double *slots = nullptr;
+    HQ_TRY(dalloc(c, (void **)&slots, c->N * sizeof(double)));
+    hoqri_status s = HOQRI_OK;
+    for (int n = 0; n < c->N && s == HOQRI_OK; ++n) {
+        // A_n and G at the current factors (Alg. 3: the core first), then the
+        // mode's term of Eq. grad2
+        s = refresh_core(c, n, nullptr);
+        if (s == HOQRI_OK) s = ttmctc_block(c, n, c->A, false);
+        if (s == HOQRI_OK) s = grad_term(c, n, c->A, slots + n);
+    }
+    std::vector<double> h(c->N, 0.0);
+    if (s == HOQRI_OK) {
+        if (cudaMemcpyAsync(h.data(), slots, c->N * sizeof(double), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_error(std::string("hoqri_grad_norm2: ") + cudaGetErrorString(cudaGetLastError()));
+            s = HOQRI_ERR_CUDA;
+        }
+    }
+    cudaStreamSynchronize(c->stream);
+    dfree(slots, c->stream);
+    c->device_bytes -= (int64_t)std::max<size_t>(c->N * sizeof(double), 16);
+    if (s != HOQRI_OK) return s;
+    HQ_TRY(check_device_error(c));
+    double g = 0.0;
+    for (int n = 0; n < c->N; ++n) g += 4.0 * h[n];
+    *out = g;
     return HOQRI_OK;
 }
 

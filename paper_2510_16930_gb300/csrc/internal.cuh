@@ -209,6 +209,8 @@ hoqri_status qr_init(hoqri_ctx *c);
 // HOQRI_FP64 or HOQRI_FP32, 1 <= K <= HOQRI_NOALLOC_MAXK, I >= K (checked by the caller)
 hoqri_status orthonormalize_noalloc(int prec, int64_t I, int K, const void *A, void *U, cudaStream_t st);
 hoqri_status orthonormalize(hoqri_ctx *c, int n, void *A_inout, void *U_out);
+// ||A_n - U_n G_(n) G_(n)^T||_F^2 in FP64 into *slot (device), G the context's core (grad.cu)
+hoqri_status grad_term(hoqri_ctx *c, int n, const void *A, double *slot);
 hoqri_status init_factors_seeded(hoqri_ctx *c);
 
 int64_t ceil_div(int64_t a, int64_t b);

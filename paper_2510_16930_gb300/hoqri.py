@@ -23,7 +23,7 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 
 # every entry point declared in include/hoqri.h
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
-           "hoqri_iterate", "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
+           "hoqri_iterate", "hoqri_run", "hoqri_grad_norm2", "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
            "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
            "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
            "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take", "hoqri_server_destroy")
@@ -73,6 +73,8 @@ def load(build_if_missing: bool = True):
     L.hoqri_ttmctc.argtypes = [vp, i32, vp]
     L.hoqri_orthonormalize.argtypes = [vp, i32, vp, vp]
     L.hoqri_iterate.argtypes = [vp, i32, C.POINTER(C.c_double)]
+    L.hoqri_run.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i32)]
+    L.hoqri_grad_norm2.argtypes = [vp, C.POINTER(C.c_double)]
     L.hoqri_get_factor.argtypes = [vp, i32, vp]
     L.hoqri_set_factor.argtypes = [vp, i32, vp]
     L.hoqri_fit.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -91,7 +93,8 @@ def load(build_if_missing: bool = True):
     L.hoqri_server_destroy.restype = None
     L.hoqri_destroy.argtypes = [vp]
     L.hoqri_destroy.restype = None
-    for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate",
+    for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate", "hoqri_run",
+                 "hoqri_grad_norm2",
                  "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_synchronize",
                  "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
                  "hoqri_server_submit", "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take"):
@@ -167,6 +170,22 @@ def hoqri_iterate(ctx, iters, want_hist=True):
     h = (C.c_double * max(int(iters), 1))() if want_hist else None
     _check(load().hoqri_iterate(ctx, int(iters), h))
     return np.array(h[:int(iters)]) if want_hist else None
+
+
+def hoqri_run(ctx, max_iters):
+    """Sweeps until the residual changes by less than the context's tol (or
+    max_iters sweeps); returns the residual history of the sweeps run."""
+    h = (C.c_double * max(int(max_iters), 1))()
+    done = C.c_int32(0)
+    _check(load().hoqri_run(ctx, int(max_iters), h, C.byref(done)))
+    return np.array(h[:done.value])
+
+
+def hoqri_grad_norm2(ctx):
+    """||grad f||^2 at the current factors (FP64)."""
+    out = C.c_double(0.0)
+    _check(load().hoqri_grad_norm2(ctx, C.byref(out)))
+    return out.value
 
 
 def hoqri_get_factor(ctx, mode, U_out):

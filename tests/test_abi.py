@@ -85,3 +85,14 @@ def test_server_rejects_bad_requests_without_gpu_work():
         hoqri.hoqri_server_destroy(srv)
     with pytest.raises(hoqri.HoqriError):
         hoqri.hoqri_server_create(0, 4)
+
+
+def test_run_and_grad_reject_a_null_context_without_gpu_work():
+    import ctypes as C
+    L = hoqri.load()
+    done = C.c_int32(-1)
+    out = C.c_double(-1.0)
+    assert L.hoqri_run(None, 3, None, C.byref(done)) == hoqri.HOQRI_ERR_INVALID
+    assert done.value == -1
+    assert L.hoqri_grad_norm2(None, C.byref(out)) == hoqri.HOQRI_ERR_INVALID
+    assert "NULL context" in hoqri.load().hoqri_last_error().decode()

@@ -301,6 +301,68 @@ def test_exact_low_rank_recovered(orc):
         assert D.proj_dist(u, ut) < 1e-7
 
 
+# ------------------------------------------------ Riemannian gradient (Sec. 5)
+
+def test_grad_two_forms_of_eq_grad2_agree(orc):
+    """Eq. grad2: sum_n ||2 A_n - 2 U_n G_(n) G_(n)^T||^2 equals
+    sum_n 4 (||A_n||^2 - ||G_(n) G_(n)^T||^2) at orthonormal U (the last line
+    follows from Eq. AU); the second form is computed here from the oracle's
+    A_n and core, independently of its gradient routine."""
+    dims, ranks = (9, 8, 7, 6), (3, 2, 3, 2)
+    idx, vals = _rand_coo(dims, 300, 40)
+    U = _rand_U(dims, ranks, 41, ortho=True)
+    g = orc.grad_norm2(dims, idx, vals, U)
+    alt = 0.0
+    for n in range(4):
+        A, G = orc.ttmctc(dims, idx, vals, U, n, return_core=True)
+        Gn = D.unfold(G, n)
+        alt += 4.0 * (float((A ** 2).sum()) - float(((Gn @ Gn.T) ** 2).sum()))
+    assert g > 0 and abs(g - alt) <= 1e-10 * g
+
+
+def test_grad_is_projected_euclidean_gradient(orc):
+    """Block n of the gradient is tangent (U_n^T grad_n = 0) and its inner
+    product with a tangent direction equals the directional derivative of the
+    dense objective f(U) = ||X x {U^T}||^2, taken by central differences."""
+    dims, ranks = (7, 6, 5), (3, 2, 2)
+    idx, vals = _rand_coo(dims, 90, 42)
+    U = _rand_U(dims, ranks, 43, ortho=True)
+    Xd = D.dense(dims, idx, vals)
+
+    def f(V):
+        return float((D.core_dense(Xd, V) ** 2).sum())
+
+    rng = np.random.default_rng(44)
+    for n in range(3):
+        gn = orc.grad(dims, idx, vals, U, n)
+        assert np.linalg.norm(U[n].T @ gn) <= 1e-12 * np.linalg.norm(gn)
+        Z = rng.standard_normal(U[n].shape)
+        S = rng.standard_normal((ranks[n], ranks[n]))
+        xi = Z - U[n] @ (U[n].T @ Z) + U[n] @ (S - S.T)  # tangent to the Stiefel manifold at U_n
+        eps = 1e-5
+        Up, Um = list(U), list(U)
+        Up[n], Um[n] = U[n] + eps * xi, U[n] - eps * xi
+        fd = (f(Up) - f(Um)) / (2 * eps)
+        assert abs(fd - float((gn * xi).sum())) <= 1e-7 * max(1.0, abs(fd))
+
+
+def test_grad_vanishes_at_stationary_points(orc):
+    """Def. stationary: zero at the planted factors of an exactly rank-K tensor,
+    and driven to zero by HOQRI from a random start (Sec. 5.2)."""
+    dims, ranks = (8, 7, 6), (2, 3, 2)
+    rng = np.random.default_rng(45)
+    Ut = [np.linalg.qr(rng.standard_normal((I, K)))[0] for I, K in zip(dims, ranks)]
+    Xd = D.reconstruct(rng.standard_normal(ranks) * 3.0, Ut)
+    grid = np.meshgrid(*[np.arange(I) for I in dims], indexing="ij")
+    idx = [g.ravel().astype(np.int32) for g in grid]
+    nx4 = float((Xd ** 2).sum()) ** 2
+    assert orc.grad_norm2(dims, idx, Xd.ravel(), Ut) <= 1e-24 * nx4
+    U0 = _rand_U(dims, ranks, 46, ortho=True)
+    g0 = orc.grad_norm2(dims, idx, Xd.ravel(), U0)
+    out = orc.hoqri(dims, idx, Xd.ravel(), U0, 30)
+    assert orc.grad_norm2(dims, idx, Xd.ravel(), out["U"]) <= 1e-10 * g0
+
+
 def test_generator_is_seeded_and_shaped():
     X1, U1, c1 = inputs.make_config("c1")
     X2, U2, c2 = inputs.make_config("c1")
