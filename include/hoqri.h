@@ -167,6 +167,19 @@ HOQRI_API hoqri_status hoqri_run(hoqri_ctx *ctx, int32_t max_iters, double *resi
  */
 HOQRI_API hoqri_status hoqri_grad_norm2(hoqri_ctx *ctx, double *out);
 
+/*
+ * Replaces every factor U_n by an orthonormal basis of the leading K_n left
+ * singular subspace of the unfolding X_(n), the HOSVD initialisation that
+ * Alg. 2 allows: orthogonal iteration on X_(n) X_(n)^T (power_iters steps,
+ * from the seeded Gaussian start of options.seed), each step
+ * Y = X_(n) (X_(n)^T V) from the nonzeros followed by the QR of the sweep.
+ * The subspace error after q steps falls like (sigma_{K+1} / sigma_K)^(2q).
+ * Temporary device memory: about 32 bytes per nonzero plus one K_n-vector per
+ * distinct column of X_(n), freed before the call returns (the call waits for
+ * its stream).  Errors: HOQRI_ERR_INVALID for power_iters < 1, HOQRI_ERR_OOM.
+ */
+HOQRI_API hoqri_status hoqri_init_hosvd(hoqri_ctx *ctx, int32_t power_iters);
+
 /* Copies the current factor U_mode (I_mode x K_mode reals) to U_out. */
 HOQRI_API hoqri_status hoqri_get_factor(hoqri_ctx *ctx, int32_t mode, void *U_out);
 

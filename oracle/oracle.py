@@ -201,6 +201,20 @@ def grad_norm2(dims, idx, vals, U):
     return float(sum(np.sum(grad(dims, idx, vals, U, n) ** 2) for n in range(len(U))))
 
 
+def hosvd(dims, idx, vals, ranks):
+    """HOSVD factors (the initialisation that Alg. 2 allows): U_n = the K_n leading
+    left singular vectors of the mode-n unfolding of X (repeated coordinates
+    summed), by LAPACK's SVD of the dense unfolding; small tensors only."""
+    X = np.zeros(tuple(int(d) for d in dims), dtype=np.float64)
+    np.add.at(X, tuple(np.asarray(a, dtype=np.int64) for a in idx), np.asarray(vals, dtype=np.float64))
+    out = []
+    for n, K in enumerate(ranks):
+        Xn = np.moveaxis(X, n, 0).reshape(X.shape[n], -1)
+        u, s, _ = np.linalg.svd(Xn, full_matrices=False)
+        out.append(u[:, :int(K)])
+    return out
+
+
 def qr(A):
     """Householder thin QR with diag(R) >= 0: returns (Q, R, zero_pivots)."""
     A = np.ascontiguousarray(A, dtype=np.float64)

@@ -668,6 +668,17 @@ hoqri_status hoqri_run(hoqri_ctx *c, int32_t max_iters, double *resid_hist, int3
     return run_sweeps(c, max_iters, c->opt.tol, resid_hist, iters_done, "hoqri_run");
 }
 
+hoqri_status hoqri_init_hosvd(hoqri_ctx *c, int32_t power_iters) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, 0));
+    if (power_iters < 1) {
+        set_error("hoqri_init_hosvd: power_iters < 1");
+        return HOQRI_ERR_INVALID;
+    }
+    HQ_TRY(init_hosvd(c, power_iters));
+    return check_device_error(c);
+}
+
 hoqri_status hoqri_grad_norm2(hoqri_ctx *c, double *out) {
     g_last_error.clear();
     HQ_TRY(check_mode(c, 0));

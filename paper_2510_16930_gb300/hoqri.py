@@ -23,7 +23,8 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 
 # every entry point declared in include/hoqri.h
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
-           "hoqri_iterate", "hoqri_run", "hoqri_grad_norm2", "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
+           "hoqri_iterate", "hoqri_run", "hoqri_grad_norm2", "hoqri_init_hosvd",
+           "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
            "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
            "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
            "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take", "hoqri_server_destroy")
@@ -75,6 +76,7 @@ def load(build_if_missing: bool = True):
     L.hoqri_iterate.argtypes = [vp, i32, C.POINTER(C.c_double)]
     L.hoqri_run.argtypes = [vp, i32, C.POINTER(C.c_double), C.POINTER(i32)]
     L.hoqri_grad_norm2.argtypes = [vp, C.POINTER(C.c_double)]
+    L.hoqri_init_hosvd.argtypes = [vp, i32]
     L.hoqri_get_factor.argtypes = [vp, i32, vp]
     L.hoqri_set_factor.argtypes = [vp, i32, vp]
     L.hoqri_fit.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -94,7 +96,7 @@ def load(build_if_missing: bool = True):
     L.hoqri_destroy.argtypes = [vp]
     L.hoqri_destroy.restype = None
     for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate", "hoqri_run",
-                 "hoqri_grad_norm2",
+                 "hoqri_grad_norm2", "hoqri_init_hosvd",
                  "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_synchronize",
                  "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
                  "hoqri_server_submit", "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take"):
@@ -186,6 +188,11 @@ def hoqri_grad_norm2(ctx):
     out = C.c_double(0.0)
     _check(load().hoqri_grad_norm2(ctx, C.byref(out)))
     return out.value
+
+
+def hoqri_init_hosvd(ctx, power_iters):
+    """Factors <- leading left singular subspaces of the unfoldings."""
+    _check(load().hoqri_init_hosvd(ctx, int(power_iters)))
 
 
 def hoqri_get_factor(ctx, mode, U_out):

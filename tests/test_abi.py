@@ -96,3 +96,7 @@ def test_run_and_grad_reject_a_null_context_without_gpu_work():
     assert done.value == -1
     assert L.hoqri_grad_norm2(None, C.byref(out)) == hoqri.HOQRI_ERR_INVALID
     assert "NULL context" in hoqri.load().hoqri_last_error().decode()
+
+
+def test_init_hosvd_rejects_a_null_context_without_gpu_work():
+    assert hoqri.load().hoqri_init_hosvd(None, 2) == hoqri.HOQRI_ERR_INVALID

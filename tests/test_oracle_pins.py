@@ -363,6 +363,38 @@ def test_grad_vanishes_at_stationary_points(orc):
     assert orc.grad_norm2(dims, idx, Xd.ravel(), out["U"]) <= 1e-10 * g0
 
 
+def test_hosvd_recovers_planted_subspaces(orc):
+    """HOSVD of an exactly rank-K tensor: the leading left singular subspaces of
+    its unfoldings are the planted factors' ranges (and the unfolding has rank
+    K_n), so the oracle's factors span them; with repeated coordinates summed."""
+    dims, ranks = (9, 8, 7), (3, 2, 3)
+    rng = np.random.default_rng(47)
+    Ut = [np.linalg.qr(rng.standard_normal((I, K)))[0] for I, K in zip(dims, ranks)]
+    Xd = D.reconstruct(rng.standard_normal(ranks), Ut)
+    grid = np.meshgrid(*[np.arange(I) for I in dims], indexing="ij")
+    idx = [np.concatenate([g.ravel(), g.ravel()[:5]]).astype(np.int32) for g in grid]
+    vals = np.concatenate([Xd.ravel(), np.zeros(5)])
+    U = orc.hosvd(dims, idx, vals, ranks)
+    for u, ut, K in zip(U, Ut, ranks):
+        assert u.shape[1] == K and np.linalg.norm(u.T @ u - np.eye(K)) < 1e-12
+        assert D.proj_dist(u, ut) < 1e-10
+
+
+def test_hosvd_is_the_top_eigenspace_of_the_unfolding_gram(orc):
+    """U_n spans the top-K_n eigenvectors of X_(n) X_(n)^T, here formed from
+    the sparse entries by brute force and diagonalised by LAPACK's symmetric
+    eigensolver, a different routine from the oracle's SVD."""
+    dims, ranks = (10, 7, 6), (3, 2, 2)
+    idx, vals = _rand_coo(dims, 120, 48)
+    U = orc.hosvd(dims, idx, vals, ranks)
+    Xd = D.dense(dims, idx, vals)
+    for n, K in enumerate(ranks):
+        Xn = D.unfold(Xd, n)
+        w, v = np.linalg.eigh(Xn @ Xn.T)
+        assert w[-K] - w[-K - 1] > 1e-6 * w[-1]  # a gap, so the subspace is unique
+        assert D.proj_dist(U[n], v[:, -K:]) < 1e-9
+
+
 def test_generator_is_seeded_and_shaped():
     X1, U1, c1 = inputs.make_config("c1")
     X2, U2, c2 = inputs.make_config("c1")
