@@ -8,9 +8,13 @@
 // X_(n)^T V has one row per distinct column of X_(n), i.e. per distinct tuple
 // of the other modes' indices among the nonzeros.  The mode-n stream is sorted
 // by row; a stable sort of its positions by that tuple groups the columns:
-//   W(c, :) = sum over the positions q of column c of x_q V(i_n(q), :)   (one thread per column)
-//   Y(i, :) = sum over the positions p of row i of x_p W(col(p), :)      (one warp per row)
-// Both sums run in a fixed order, so the result is the same on every run.
+//   W(c, :) = sum over the positions q of column c of x_q V(i_n(q), :)
+//   Y(i, :) = sum over the positions p of row i of x_p W(col(p), :)
+// Both are segmented sums over skewed segments (Zipf rows and columns hold up
+// to millions of positions), so each segment is cut into pieces of at most
+// HS_PIECE positions: one warp sums a piece (lanes take every 32nd position,
+// then a fixed butterfly), and a second kernel adds the pieces of each segment
+// in order.  The order is fixed, so the result is the same on every run.
 #include <cub/cub.cuh>
 
 #include <algorithm>
@@ -80,61 +84,73 @@ __global__ void k_hs_rows(const int64_t *row_ptr, const int32_t *row_id, int64_t
     }
 }
 
-// W(c, :) = sum_{q in column c} x V(i_n, :), K columns in chunks of HS_KCH
-template <typename T>
-__global__ void __launch_bounds__(HS_TPB) k_hs_w(const int64_t *col_start, int64_t ncol, const int32_t *perm,
-                                                 const T *vals, const int32_t *in_of, const T *V, int K, T *W) {
-    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncol; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q0 = col_start[c], q1 = col_start[c + 1];
-        for (int kc = 0; kc < K; kc += HS_KCH) {
-            T acc[HS_KCH];
-#pragma unroll
-            for (int k = 0; k < HS_KCH; ++k) acc[k] = T(0);
-            for (int64_t q = q0; q < q1; ++q) {
-                const int32_t p = perm[q];
-                const T x = vals[p];
-                const T *v = V + (int64_t)in_of[p] * K + kc;
-#pragma unroll
-                for (int k = 0; k < HS_KCH; ++k)
-                    if (kc + k < K) acc[k] += x * v[k];
-            }
-#pragma unroll
-            for (int k = 0; k < HS_KCH; ++k)
-                if (kc + k < K) W[c * K + kc + k] = acc[k];
-        }
+constexpr int64_t HS_PIECE = 4096;  // positions per piece of a segment
+
+// pieces per segment: max(1, ceil(len / HS_PIECE))
+__global__ void k_hs_piece_count(const int64_t *off, int64_t nseg, int32_t *cnt) {
+    for (int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sg < nseg; sg += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t len = off[sg + 1] - off[sg];
+        const int64_t np = (len + HS_PIECE - 1) / HS_PIECE;
+        cnt[sg] = (int32_t)(np > 1 ? np : 1);
     }
 }
 
-// Y(row_id[r], :) = sum_{p in row r} x W(col(p), :): one warp per row, lanes
-// take every 32nd position, then a fixed butterfly over the lanes
+// piece -> (segment, index within the segment)
+__global__ void k_hs_piece_fill(const int32_t *cnt, const int32_t *poff, int64_t nseg, int32_t *pseg, int32_t *pj) {
+    for (int64_t sg = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sg < nseg; sg += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < cnt[sg]; ++j) {
+            pseg[poff[sg] + j] = (int32_t)sg;
+            pj[poff[sg] + j] = j;
+        }
+}
+
+// part(piece, :) = sum over the piece's positions q of x_p Gm(gidx(p), :), with
+// p = pmap(q) (pmap NULL: p = q); one warp per piece, K in chunks of HS_KCH
 template <typename T>
-__global__ void __launch_bounds__(HS_TPB) k_hs_y(const int64_t *row_ptr, const int32_t *row_id, int64_t R,
-                                                 const T *vals, const int32_t *col_of, const T *W, int K, T *Y) {
+__global__ void __launch_bounds__(HS_TPB) k_hs_pieces(const int64_t *off, const int32_t *pseg, const int32_t *pj,
+                                                      int64_t npiece, const int32_t *pmap, const T *vals,
+                                                      const int32_t *gidx, const T *Gm, int K, T *part) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; r < R; r += warps) {
-        const int64_t p0 = row_ptr[r], p1 = row_ptr[r + 1];
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < npiece; w += warps) {
+        const int64_t sg = pseg[w];
+        const int64_t q0 = off[sg] + (int64_t)pj[w] * HS_PIECE;
+        const int64_t q1 = min(off[sg + 1], q0 + HS_PIECE);
         for (int kc = 0; kc < K; kc += HS_KCH) {
             T acc[HS_KCH];
 #pragma unroll
             for (int k = 0; k < HS_KCH; ++k) acc[k] = T(0);
-            for (int64_t p = p0 + lane; p < p1; p += 32) {
+            for (int64_t q = q0 + lane; q < q1; q += 32) {
+                const int64_t p = pmap ? (int64_t)pmap[q] : q;
                 const T x = vals[p];
-                const T *w = W + (int64_t)col_of[p] * K + kc;
+                const T *g = Gm + (int64_t)gidx[p] * K + kc;
 #pragma unroll
                 for (int k = 0; k < HS_KCH; ++k)
-                    if (kc + k < K) acc[k] += x * w[k];
+                    if (kc + k < K) acc[k] += x * g[k];
             }
 #pragma unroll
             for (int k = 0; k < HS_KCH; ++k)
                 for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
             if (lane == 0) {
-                T *y = Y + (int64_t)row_id[r] * K + kc;
 #pragma unroll
                 for (int k = 0; k < HS_KCH; ++k)
-                    if (kc + k < K) y[k] = acc[k];
+                    if (kc + k < K) part[w * K + kc + k] = acc[k];
             }
         }
+    }
+}
+
+// out(dst(s), :) = sum of the pieces of segment s in order; dst = s when
+// dst_id is NULL
+template <typename T>
+__global__ void k_hs_combine(const int32_t *cnt, const int32_t *poff, int64_t nseg, const T *part, int K,
+                             const int32_t *dst_id, T *out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nseg * K; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t sg = t / K;
+        const int k = (int)(t - sg * K);
+        T s = T(0);
+        for (int j = 0; j < cnt[sg]; ++j) s += part[(int64_t)(poff[sg] + j) * K + k];
+        out[(dst_id ? (int64_t)dst_id[sg] : sg) * K + k] = s;
     }
 }
 
@@ -215,20 +231,62 @@ hoqri_status hosvd_mode(hoqri_ctx *c, int n, int power_iters) {
         k_hs_rows<<<G, HS_TPB, 0, st>>>(M.row_ptr, M.row_id, M.R, nnz, in_of);
         perm = src;
     }
-    T *W;
-    HQ_TRY(tmp.get(&W, (size_t)std::max<int64_t>(ncol, 1) * K));
     T *V = static_cast<T *>(c->U[n]);
     T *Y = static_cast<T *>(c->A);
-    const int Gw = hs_grid(ncol, c->num_sms);
-    const int Gy = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(M.R, 1), HS_TPB / 32),
-                                                              (int64_t)c->num_sms * 16));
-    for (int it = 0; it < power_iters; ++it) {
-        HQ_CUDA(cudaMemsetAsync(Y, 0, (size_t)I * K * sizeof(T), st));
-        if (nnz > 0) {
-            k_hs_w<T><<<Gw, HS_TPB, 0, st>>>(col_start, ncol, perm, static_cast<const T *>(M.vals), in_of, V, K, W);
-            k_hs_y<T><<<Gy, HS_TPB, 0, st>>>(M.row_ptr, M.row_id, M.R, static_cast<const T *>(M.vals), col_of, W, K, Y);
-            c->nlaunch += 2;
+    if (nnz == 0) {
+        // X_(n) = 0: the QR of a zero Y completes an orthonormal basis
+        for (int it = 0; it < power_iters; ++it) {
+            HQ_CUDA(cudaMemsetAsync(Y, 0, (size_t)I * K * sizeof(T), st));
+            HQ_TRY(orthonormalize(c, n, Y, V));
         }
+        HQ_CUDA(cudaStreamSynchronize(st));
+        return HOQRI_OK;
+    }
+    // pieces of the columns (column-sorted positions) and of the rows
+    struct Pieces {
+        int32_t *cnt = nullptr, *poff = nullptr, *pseg = nullptr, *pj = nullptr;
+        int64_t n = 0;
+    };
+    auto make_pieces = [&](const int64_t *off, int64_t nseg, Pieces *pc) -> hoqri_status {
+        HQ_TRY(tmp.get(&pc->cnt, nseg));
+        HQ_TRY(tmp.get(&pc->poff, nseg));
+        const int g = hs_grid(nseg, c->num_sms);
+        k_hs_piece_count<<<g, HS_TPB, 0, st>>>(off, nseg, pc->cnt);
+        size_t tb = 0;
+        HQ_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tb, pc->cnt, pc->poff, (int)nseg, st));
+        char *t;
+        HQ_TRY(tmp.get(&t, tb));
+        HQ_CUDA(cub::DeviceScan::ExclusiveSum(t, tb, pc->cnt, pc->poff, (int)nseg, st));
+        int32_t h[2] = {0, 0};
+        HQ_CUDA(cudaMemcpyAsync(&h[0], pc->poff + nseg - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        HQ_CUDA(cudaMemcpyAsync(&h[1], pc->cnt + nseg - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        HQ_CUDA(cudaStreamSynchronize(st));
+        pc->n = (int64_t)h[0] + h[1];
+        HQ_TRY(tmp.get(&pc->pseg, pc->n));
+        HQ_TRY(tmp.get(&pc->pj, pc->n));
+        k_hs_piece_fill<<<g, HS_TPB, 0, st>>>(pc->cnt, pc->poff, nseg, pc->pseg, pc->pj);
+        return HOQRI_OK;
+    };
+    Pieces pcol, prow;
+    HQ_TRY(make_pieces(col_start, ncol, &pcol));
+    HQ_TRY(make_pieces(M.row_ptr, M.R, &prow));
+    T *W, *part;
+    HQ_TRY(tmp.get(&W, (size_t)ncol * K));
+    HQ_TRY(tmp.get(&part, (size_t)std::max(pcol.n, prow.n) * K));
+    auto warp_grid = [&](int64_t pieces) {
+        return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(pieces, HS_TPB / 32), (int64_t)c->num_sms * 16));
+    };
+    const T *vals = static_cast<const T *>(M.vals);
+    for (int it = 0; it < power_iters; ++it) {
+        // W = X_(n)^T V over the columns, then Y = X_(n) W over the rows
+        k_hs_pieces<T><<<warp_grid(pcol.n), HS_TPB, 0, st>>>(col_start, pcol.pseg, pcol.pj, pcol.n, perm, vals, in_of,
+                                                             V, K, part);
+        k_hs_combine<T><<<hs_grid(ncol * K, c->num_sms), HS_TPB, 0, st>>>(pcol.cnt, pcol.poff, ncol, part, K, nullptr, W);
+        HQ_CUDA(cudaMemsetAsync(Y, 0, (size_t)I * K * sizeof(T), st));
+        k_hs_pieces<T><<<warp_grid(prow.n), HS_TPB, 0, st>>>(M.row_ptr, prow.pseg, prow.pj, prow.n, nullptr, vals,
+                                                             col_of, W, K, part);
+        k_hs_combine<T><<<hs_grid(M.R * K, c->num_sms), HS_TPB, 0, st>>>(prow.cnt, prow.poff, M.R, part, K, M.row_id, Y);
+        c->nlaunch += 4;
         HQ_TRY(orthonormalize(c, n, Y, V));
     }
     HQ_CUDA(cudaGetLastError());
