@@ -681,7 +681,6 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
     cudaStream_t st = c->stream;
     const int nb = gram_blocks(I, c->num_sms);
     const int64_t rpb = ceil_div(I, nb);
-    const int npairs = K * (K + 1) / 2;
     double *Rd = c->qr_small;
     const int apply_rows_grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(I, 256), (int64_t)c->num_sms * 8));
     // flag 0: CholeskyQR2; flag 1 (qr_kind 1): Householder from the start; no
@@ -697,7 +696,6 @@ hoqri_status orthonormalize_t(hoqri_ctx *c, int n, T *A, T *U) {
         launch_apply<T>(st, c->dflag, pass, src, I, K, Rd, pass == 0 ? A : U, apply_rows_grid);
         c->nlaunch += 4;
     }
-    (void)npairs;
     HQ_CUDA(cudaGetLastError());
     return HOQRI_OK;
 }
