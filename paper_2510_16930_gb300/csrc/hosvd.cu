@@ -21,6 +21,7 @@
 #include <string>
 #include <vector>
 
+#include "hosvd.cuh"
 #include "internal.cuh"
 
 namespace hoqri {

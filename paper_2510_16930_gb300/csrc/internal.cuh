@@ -211,8 +211,6 @@ hoqri_status orthonormalize_noalloc(int prec, int64_t I, int K, const void *A, v
 hoqri_status orthonormalize(hoqri_ctx *c, int n, void *A_inout, void *U_out);
 // ||A_n - U_n G_(n) G_(n)^T||_F^2 in FP64 into *slot (device), G the context's core (grad.cu)
 hoqri_status grad_term(hoqri_ctx *c, int n, const void *A, double *slot);
-// factors <- leading left singular subspaces of the unfoldings (hosvd.cu)
-hoqri_status init_hosvd(hoqri_ctx *c, int power_iters);
 hoqri_status init_factors_seeded(hoqri_ctx *c);
 
 int64_t ceil_div(int64_t a, int64_t b);
