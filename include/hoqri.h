@@ -59,7 +59,7 @@ typedef enum {
     HOQRI_ERR_QR_BREAKDOWN = 4, /* Cholesky breakdown with the fallback disabled */
     HOQRI_ERR_RANK = 5,         /* K_n > I_n or K_n > prod_{m != n} K_m */
     HOQRI_ERR_TIMEOUT = 6,      /* a bounded device wait ran out */
-    HOQRI_ERR_UNSUPPORTED = 7   /* shape or precision outside this build's kernels */
+    HOQRI_ERR_UNSUPPORTED = 7   /* shape or precision outside the library's kernels */
 } hoqri_status;
 
 typedef enum {

@@ -698,7 +698,7 @@ hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem)
         HQ_GEN(32)
         HQ_GEN(64)
         default:
-            set_error("P_{-n} = prod_{m != n} K_m above 2048 is not supported by this build");
+            set_error("P_{-n} = prod_{m != n} K_m above 2048 is not supported by the library's kernels");
             return HOQRI_ERR_UNSUPPORTED;
     }
 #undef HQ_GEN
