@@ -187,9 +187,11 @@ HOQRI_API hoqri_status hoqri_get_factor(hoqri_ctx *ctx, int32_t mode, void *U_ou
  * orthonormal). */
 HOQRI_API hoqri_status hoqri_set_factor(hoqri_ctx *ctx, int32_t mode, const void *U_in);
 
-/* Residual of the last core computed (by hoqri_core, hoqri_ttmctc or
- * hoqri_iterate): resid as in hoqri_iterate, ||X||^2 and ||G||^2 in FP64.  Any
- * output pointer may be NULL (host pointers). */
+/* Residual of the last core computed (by hoqri_core, hoqri_ttmctc,
+ * hoqri_iterate, hoqri_run or hoqri_grad_norm2; not by hoqri_set_factor or
+ * hoqri_init_hosvd, which change the factors only): resid as in hoqri_iterate,
+ * ||X||^2 and ||G||^2 in FP64.  Any output pointer may be NULL (host
+ * pointers). */
 HOQRI_API hoqri_status hoqri_fit(hoqri_ctx *ctx, double *resid, double *normX2, double *normG2);
 
 /* Sizes after set-up (host pointers, each may be NULL): nnz after summing
