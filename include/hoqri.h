@@ -239,11 +239,15 @@ HOQRI_API hoqri_status hoqri_synchronize(hoqri_ctx *ctx);
  * call sets its flags to zero itself (cudaMemsetAsync on the stream);
  * the partials and R^{-1} are fully written before they are read, so nothing
  * needs to start at zero.  Its address is looked up with cudaGetSymbolAddress
- * on the first call made on each device (cached afterwards); that first call
- * must come before any stream capture on the device begins.  Calls whose
+ * on every call, on the device current at the call.  Under lazy module
+ * loading the first call on a device loads the library's device code, which
+ * reserves the array (and the module's other memory) at that point: make one
+ * call during set-up if later calls must not reserve anything.  Calls whose
  * work overlaps in time (different streams, or different host threads) share
  * the one scratch array and race: order them on one stream.
- * The call waits for the stream to finish, since it reads the breakdown flag.
+ * The call copies the breakdown flag to the host and waits for the stream,
+ * so it may not be called while its stream, or any stream under global
+ * capture, is being captured into a CUDA graph.
  * Errors: HOQRI_ERR_INVALID for a precision other than the two above, K out of
  * range (the message names the limit), I < K, host or overlapping buffers;
  * HOQRI_ERR_QR_BREAKDOWN when a Cholesky pivot is not clearly positive after

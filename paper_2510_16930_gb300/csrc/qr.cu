@@ -755,10 +755,12 @@ constexpr int NA_MAX_DEVICES = 64;
 static __device__ __align__(256) unsigned char g_na_scratch[HOQRI_NOALLOC_SCRATCH_BYTES];
 
 std::mutex g_na_mu;
-unsigned char *g_na_addr[NA_MAX_DEVICES];
 int g_na_sms[NA_MAX_DEVICES];
 
-// address of the scratch on the current device: looked up once per device
+// Address of the scratch on the current device.  It is looked up on every
+// call (cheap once the module is loaded): a cached address would go stale if
+// the caller reset the device, which reloads the module and may move the array.
+// Only the SM count is cached per device.
 hoqri_status na_scratch(unsigned char **p, int *sms) {
     int dev = 0;
     HQ_CUDA(cudaGetDevice(&dev));
@@ -767,17 +769,18 @@ hoqri_status na_scratch(unsigned char **p, int *sms) {
                   std::to_string(NA_MAX_DEVICES - 1));
         return HOQRI_ERR_INVALID;
     }
-    std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
-        void *a = nullptr;
-        HQ_CUDA(cudaGetSymbolAddress(&a, g_na_scratch));
-        int n = 0;
-        HQ_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-        g_na_sms[dev] = std::max(n, 1);
-        g_na_addr[dev] = static_cast<unsigned char *>(a);
+    void *a = nullptr;
+    HQ_CUDA(cudaGetSymbolAddress(&a, g_na_scratch));
+    {
+        std::lock_guard<std::mutex> lk(g_na_mu);
+        if (g_na_sms[dev] == 0) {
+            int n = 0;
+            HQ_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+            g_na_sms[dev] = std::max(n, 1);
+        }
+        *sms = g_na_sms[dev];
     }
-    *p = g_na_addr[dev];
-    *sms = g_na_sms[dev];
+    *p = static_cast<unsigned char *>(a);
     return HOQRI_OK;
 }
 

@@ -61,6 +61,30 @@ def test_ttmctc_and_core_match_oracle(orc, shape, chunk, prec):
         assert rel(G, G_ref) <= TOL[prec]
 
 
+@pytest.mark.parametrize("chunk", [0, 96])
+@pytest.mark.parametrize("shape", SHAPES, ids=[str(s[0]) for s in SHAPES])
+def test_o_ik_form_matches_oracle(orc, shape, chunk):
+    """The O(IK)-memory form of Table 2 (one_stream = 2: a separate core pass
+    over the nonzeros, no stored Y_(n)) for FP32, every shape, against Alg. 3."""
+    dims, ranks, nnz, dist = shape
+    X, U0 = _case(dims, ranks, nnz, 1234 + nnz, dist=dist)
+    vals = X.vals.astype(np.float32)
+    U0c = [u.astype(np.float32) for u in U0]
+    U0o = [u.astype(np.float64) for u in U0c]
+    vo = vals.astype(np.float64)
+    with Ctx(dims, X.idx, vals, U0c, FP32, chunk=chunk, one_stream=2) as c:
+        _, _, dev_bytes = c.info()
+        for n in range(len(dims)):
+            A_ref, G_ref = orc.ttmctc(dims, X.idx, vo, U0o, n, return_core=True)
+            A = c.ttmctc(n)
+            assert rel(A, A_ref) <= TOL[FP32], (n, rel(A, A_ref))
+        G = c.core()
+        assert rel(G, G_ref) <= TOL[FP32]
+    # no Y_(n) is held: the context is no larger than the one-stream form's
+    with Ctx(dims, X.idx, vals, U0c, FP32, chunk=chunk) as c1:
+        assert dev_bytes <= c1.info()[2]
+
+
 def test_fit_and_nnz_after_coalescing(orc):
     dims, ranks = (50, 40, 30), (4, 4, 3)
     X, U0 = _case(dims, ranks, 6000, 77)
