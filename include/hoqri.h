@@ -83,8 +83,10 @@ typedef struct {
     int32_t use_graphs; /* 1: hoqri_iterate replays one sweep as a CUDA graph */
     int32_t one_stream; /* 0/1: FP32 modes with a register-tile plan stream their nonzeros
                            once per block update and keep Y_(n) (R_n x P_{-n} floats) for
-                           the core G = U_n^T Y_(n); 2: the paper's O(IK) memory form
-                           (separate core pass, no Y) */
+                           the core G = U_n^T Y_(n) (sliced pass); 2: the paper's O(IK)
+                           memory form (separate core pass, no Y); 3: as 0, through the
+                           fiber-factored pass where the shape has one (order 3 or 4,
+                           other ranks powers of two >= 4, P_{-n} <= 1024) */
     uint64_t seed;      /* seed of the initial factors when U0 is NULL */
     double tol;         /* hoqri_run: stop after the first sweep whose residual differs
                            from the previous one by less than tol (0: never) */

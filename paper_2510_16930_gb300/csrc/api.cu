@@ -114,6 +114,13 @@ static void destroy_impl(hoqri_ctx *c) {
         dfree(M.item_e, st);
         dfree(M.item_aux, st);
         dfree(M.span, st);
+        dfree(M.fb_pstart, st);
+        dfree(M.fb_plenf, st);
+        dfree(M.fb_pa, st);
+        dfree(M.fb_pb, st);
+        dfree(M.fb_prange, st);
+        dfree(M.fb_rrow0, st);
+        dfree(M.fb_span, st);
         dfree(c->U[n], st);
     }
     dfree(c->gslot, st);
@@ -130,6 +137,7 @@ static void destroy_impl(hoqri_ctx *c) {
     dfree(c->gnorm_part, st);
     dfree(c->Y, st);
     dfree(c->ypart, st);
+    dfree(c->fpart, st);
     dfree(c->usplit, st);
     dfree(c->claim, st);
     cudaGetLastError();

@@ -970,14 +970,23 @@ __global__ void k_split_bf16(const float *U, int64_t rows, int K, uint32_t *out)
 
 template <int NM1>
 hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, const HybLaunch &L) {
-    // two blocks of HY_WARPS warps per SM: part 0 (long rows), then part 1 (slices)
-    const int grid = HY_BLOCKS_PER_SM * c->num_sms;
+    // hyb_blocks_per_sm blocks of HY_WARPS warps per SM: part 0 (long rows), then part 1 (slices)
+    const int grid = hyb_blocks_per_sm(p) * c->num_sms;
+    // shared-memory share of the SM's unified L1 / shared store: just what the
+    // resident blocks need, so the rest stays L1 for the factor rows of the most
+    // frequent indices (a skewed index law gathers most rows from a few thousand)
+    int smem_sm = 0;
+    HQ_CUDA(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device));
+    const int carve = (int)std::min<int64_t>(
+        100, ceil_div((int64_t)hyb_blocks_per_sm(p) * ((int64_t)L.smem + 1024) * 100, std::max(smem_sm, 1)));
 #define HQ_HYB(TLV, TVV, MTV, NTV)                                                                           \
     if (p.TL == TLV && p.TV == TVV && L.MT == MTV && L.NT == NTV) {                                          \
         auto k0 = k_hyb<NM1, TLV, TVV, MTV, NTV, 0>;                                                         \
         auto k1 = k_hyb<NM1, TLV, TVV, 0, 0, 1>;                                                             \
         HQ_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
         HQ_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
+        HQ_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributePreferredSharedMemoryCarveout, carve));           \
+        HQ_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, carve));           \
         if (a.nitem_long > 0) {                                                                              \
             k0<<<grid, HY_WARPS * 32, L.smem, c->stream>>>(a);                                               \
             c->nlaunch++;                                                                                    \
@@ -1013,15 +1022,23 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
 
 }  // namespace
 
-bool hyb_mode(const hoqri_ctx *c, int n) { return c->ms[n].hyb && c->Y != nullptr; }
+bool hyb_tile(const hoqri_ctx *c, int n, FastTile *out) { return fast_tile(c, n, out); }
+
+int hyb_blocks_per_sm(const FastTile &p) {
+    (void)p;
+    return 2;
+}
+
+bool hyb_mode(const hoqri_ctx *c, int n) { return (c->ms[n].hyb || c->ms[n].fib) && c->Y != nullptr; }
 
 // The pass over mode n's hybrid stream: writes every row y_r of Y_(n) into the
 // dense R_n x P_{-n} buffer c->Y (rows cut by task boundaries are completed by
 // k_span_fix).
 hoqri_status hyb_pass(hoqri_ctx *c, int n) {
+    if (c->ms[n].fib) return fib_pass(c, n);
     const ModeStore &M = c->ms[n];
     FastTile p;
-    if (!fast_tile(c, n, &p)) {
+    if (!hyb_tile(c, n, &p)) {
         set_error("hybrid pass: mode has no register-tile plan");
         return HOQRI_ERR_UNSUPPORTED;
     }
@@ -1187,7 +1204,7 @@ hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
 
 size_t hyb_smem_need(const hoqri_ctx *c, int n) {
     FastTile p;
-    if (!fast_tile(c, n, &p)) return (size_t)-1;
+    if (!hyb_tile(c, n, &p)) return (size_t)-1;
     return hyb_launch(c, n, p).smem;
 }
 

@@ -13,8 +13,8 @@
 
 #define HOQRI_MAXN 8
 #define HOQRI_MAXK 64
-// blocks of the hybrid pass kernel per SM (8 warps each); the work ranges of
-// its long rows are cut for HY_BLOCKS_PER_SM * 8 warps per SM
+// most blocks of the hybrid pass kernel per SM (8 warps each); the work
+// ranges of its long rows are cut for hyb_blocks_per_sm() * 8 warps per SM
 #define HY_BLOCKS_PER_SM 2
 
 namespace hoqri {
@@ -44,6 +44,13 @@ struct Status {
     } while (0)
 
 // ------------------------------------------------------- per-mode storage
+
+// kernel and shape of the fiber-factored pass of one mode (fiber.cu)
+struct FibShapeSel {
+    int nm1 = 0, KA = 0, KB = 1, KL = 0, PP = 0;
+    const void *fn = nullptr;  // k_fib<nm1, PP, KL>
+    int warp_floats = 0;       // its shared memory per warp (4-byte words)
+};
 
 // Nonzeros sorted by their mode-n index (stable from the coalesced,
 // lexicographic order), stored as structure of arrays.
@@ -90,6 +97,23 @@ struct ModeStore {
     int64_t tune_Lshort = 0, tune_T = 0; // the layout parameters it was built with
     int64_t long_elems = 0;              // nonzeros in the long part
     int64_t hyb_bytes = 0;               // device bytes of the hybrid arrays
+
+    // Fiber-factored layout (fiber.cu) over the sorted stream above: pieces of at
+    // most FB_LP nonzeros of one fiber (run of equal prefix indices in a row), in
+    // stream order; contiguous piece ranges per warp.
+    bool fib = false;
+    FibShapeSel fb_sel;
+    int64_t fb_np = 0;                   // pieces
+    int32_t *fb_pstart = nullptr;        // [np] first sorted position
+    uint32_t *fb_plenf = nullptr;        // [np] length | first-piece-of-row bit
+    int32_t *fb_pa = nullptr, *fb_pb = nullptr;  // [np] prefix indices
+    int fb_W = 0, fb_grid = 0;           // ranges (one per warp) and CTAs
+    size_t fb_smem = 0;
+    int32_t *fb_prange = nullptr;        // [W+1]
+    int32_t *fb_rrow0 = nullptr;         // [W] compact row of each range's first piece
+    int64_t fb_nspan = 0;
+    int32_t *fb_span = nullptr;          // [3*nspan] (row, first range, last range) of cut rows
+    int64_t fb_bytes = 0;
 };
 
 struct Workspace;  // defined in the pass unit
@@ -136,6 +160,8 @@ struct hoqri_ctx {
     int64_t Y_bytes = 0;
     float *ypart = nullptr;             // [nitem_long][2][P_{-n}] pieces of rows cut by long tasks
     int64_t ypart_bytes = 0;
+    float *fpart = nullptr;             // [W][2][P_{-n}] rows cut by the fiber pass's ranges
+    int64_t fpart_bytes = 0;
     int core_grid = 0;                  // CTAs of the core pass (fixed per context)
     int pass_grid = 0;
     int core_grid_fast = 0;             // the same for the register-tiled FP32 kernels
@@ -187,6 +213,10 @@ struct FastTile {
     int Ka = 0, Kb = 0, Kl = 0, Pm = 0;
 };
 bool fast_tile(const hoqri_ctx *c, int n, FastTile *out);
+// tile of the hybrid (sliced) pass for mode n: the plan above with at most 32
+// FP32 accumulators per lane where the shape allows (three blocks per SM)
+bool hyb_tile(const hoqri_ctx *c, int n, FastTile *out);
+int hyb_blocks_per_sm(const FastTile &p);
 
 // passes (passes.cu)
 hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *normG2_slot);
@@ -199,6 +229,12 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out);
 hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk);
 size_t hyb_smem_need(const hoqri_ctx *c, int n);
 size_t hyb_smem_cap();
+// fiber-factored pass (fiber.cu): supported shape, layout, cut-row buffer size, pass
+bool fib_shape(const hoqri_ctx *c, int n, FibShapeSel *sel);
+hoqri_status build_fiber(hoqri_ctx *c, int n);
+void free_fiber(hoqri_ctx *c, int n);
+int64_t fib_part_bytes(const hoqri_ctx *c, int n);
+hoqri_status fib_pass(hoqri_ctx *c, int n);
 hoqri_status passes_init(hoqri_ctx *c);
 hoqri_status core_pass(hoqri_ctx *c, int n, void *G_out, double *normG2_slot);
 hoqri_status ttmctc_pass(hoqri_ctx *c, int n, const void *G, void *A_out);

@@ -968,9 +968,18 @@ hoqri_status passes_init(hoqri_ctx *c) {
     // ~16 work items per resident warp (8 warps per SM) for balance across SMs
     const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 128)));
     const int64_t T32 = (Tt + 31) & ~(int64_t)31;
+    int64_t fpb = 0;
     for (int n = 0; n < c->N; ++n) {
+        if (c->opt.one_stream == 2) continue;
+        if (c->opt.one_stream == 3 && fib_shape(c, n, nullptr)) {
+            // fiber-factored pass: the mode-n sorted stream plus piece descriptors
+            HQ_TRY(build_fiber(c, n));
+            ybytes = std::max<int64_t>(ybytes, c->ms[n].R * (c->P / c->K[n]) * 4);
+            fpb = std::max<int64_t>(fpb, fib_part_bytes(c, n));
+            continue;
+        }
         FastTile p;
-        if (!fast_tile(c, n, &p) || c->opt.one_stream == 2) continue;
+        if (!hyb_tile(c, n, &p)) continue;
         if (hyb_smem_need(c, n) > hyb_smem_cap()) continue;
         HQ_TRY(build_hybrid(c, n, 256, T32, 32 / p.lpn));
         const ModeStore &M = c->ms[n];
@@ -986,8 +995,16 @@ hoqri_status passes_init(hoqri_ctx *c) {
     if (ybytes > 0 && c->opt.one_stream != 2 && ybytes <= ybudget) {
         HQ_TRY(dalloc(c, (void **)&c->Y, ybytes));
         c->Y_bytes = ybytes;
-        HQ_TRY(dalloc(c, (void **)&c->ypart, ypb));
+        HQ_TRY(dalloc(c, (void **)&c->ypart, std::max<int64_t>(ypb, 16)));
         c->ypart_bytes = ypb;
+        if (fpb > 0) {
+            HQ_TRY(dalloc(c, (void **)&c->fpart, fpb));
+            c->fpart_bytes = fpb;
+        }
+    } else {
+        // no Y buffer: the modes fall back to the two-pass kernels
+        for (int n = 0; n < c->N; ++n)
+            if (c->ms[n].fib) free_fiber(c, n);
     }
     HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((c->P + 31) / 32 + 1) * sizeof(double)));
     HQ_TRY(dalloc(c, (void **)&c->claim, sizeof(unsigned long long)));

@@ -491,7 +491,9 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     // work items: the long part in items of TL elements (at least T8, and at
     // least an equal share per warp of the pass, so a warp's range is one item
     // and its windows run on across the rows of the range), then runs of slices
-    const int64_t W = (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8;
+    FastTile tile;
+    const int bps = hyb_tile(c, n, &tile) ? hyb_blocks_per_sm(tile) : HY_BLOCKS_PER_SM;
+    const int64_t W = (int64_t)c->num_sms * bps * 8;
     const int64_t TL = std::max<int64_t>(T8, ((total_long + W - 1) / W + 31) & ~(int64_t)31);
     std::vector<int64_t> is, ie;
     std::vector<int32_t> ia, span;

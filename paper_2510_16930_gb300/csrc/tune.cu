@@ -87,9 +87,9 @@ hoqri_status autotune_hybrid(hoqri_ctx *c) {
     load_file();
     for (int n = 0; n < c->N; ++n) {
         ModeStore &M = c->ms[n];
-        if (!hyb_mode(c, n)) continue;
+        if (!hyb_mode(c, n) || !M.hyb) continue;
         FastTile p;
-        if (!fast_tile(c, n, &p)) continue;
+        if (!hyb_tile(c, n, &p)) continue;
         const int SW = 32 / p.lpn;
         const int64_t T0 = M.tune_T, L0 = M.tune_Lshort;
         const double long_share = c->nnz > 0 ? (double)M.long_elems / (double)c->nnz : 0.0;
