@@ -8,6 +8,20 @@ counted after summing repeated coordinates.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--config c2] [--impl ours|reference]
 
+The JSON line of the main workload carries, besides the contract's keys, one
+object per further leg (each can be skipped with --legs):
+  forms    FP64 / FP32 / split-BF16 on the main workload for its full sweep
+           count: per-sweep fit error against FP64, throughput, sampled A_n
+           rows and core entries against the oracle;
+  c3       the same on the order-4, 1e8-nonzero mixed-precision workload;
+  c4       the planted-Tucker workload: fit and subspace distance to the
+           planted factors, FP32 and split-BF16 against FP64;
+  sweeps   the synthetic experiments of Sec. 6.1 (dimension, nnz, rank and
+           order sweeps; per-iteration time on the GPU and of the oracle);
+  serve    the serving stream (Poisson arrivals of the request mix) through
+           the request server against the same requests run one after another
+           as plain contexts;
+  hosvd    the HOSVD start on the main workload.
 --impl reference times the FP64 CPU oracle (the stand-in for the paper's CPU
 implementation) on the host cores on a bounded sample of the same workload.
 With --gpus N > 1 (launched by torchrun) every rank runs an independent
@@ -32,6 +46,10 @@ sys.path.insert(0, ROOT)
 METRIC = "TTMcTC nnz/s & roofline %, mixed vs FP32 plain at fit err≤1e-6; serve p50/p99"
 UNIT = "nnz/s"
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM (4 SMSPs x 32)
+# the serving leg's mix keeps P_{-n} <= 2048 (larger Kronecker rows run on the
+# column-blocked two-pass kernels, which the library supports but which would
+# make the 2000-request stream take many minutes)
+SERVE_MAX_PM = 2048
 
 
 def parse():
@@ -48,9 +66,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hosvd", action="store_true", help="skip the HOSVD-initialisation timing")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-vs-FP32 comparison")
-    ap.add_argument("--serve-requests", type=int, default=120,
+    ap.add_argument("--no-mixed", action="store_true", help="skip the precision legs (forms, c3, c4)")
+    ap.add_argument("--legs", default="forms,c3,c4,sweeps,serve,hosvd",
+                    help="comma list of the legs to run after the main measurement")
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving mix to stream through the server (0: skip)")
+    ap.add_argument("--one-stream", type=int, default=0, help="hoqri_options.one_stream of the main workload")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -204,14 +225,21 @@ def cpu_oracle_rate(X, U0, target_s, max_sample=None):
         return time.perf_counter() - t0
 
     # a sweep costs a fixed part (the QR of every factor) plus a part per
-    # nonzero: two calibration runs give both, then S is sized for target_s
+    # nonzero: two calibration runs give both, then S is sized for target_s;
+    # the second run is long enough (>= 0.3 s) for its time to mean something,
+    # and S is capped at 30x it, so a noisy slope cannot ask for the whole tensor
     S1 = min(2000, X.nnz)
     t1 = run(S1)
     S2 = min(X.nnz, 8 * S1)
     t2 = run(S2)
-    slope = max((t2 - t1) / max(S2 - S1, 1), 1e-9)
+    while t2 < 0.3 and S2 < X.nnz:
+        S2 = min(X.nnz, 4 * S2)
+        t2 = run(S2)
+    slope = (t2 - t1) / max(S2 - S1, 1)
+    if slope <= 0:
+        slope = t2 / S2
     fixed = max(t1 - slope * S1, 0.0)
-    S = int(min(X.nnz, max(S2, (target_s - fixed) / slope)))
+    S = int(min(X.nnz, 30 * S2, max(S2, (target_s - fixed) / slope)))
     if max_sample:
         S = min(S, max_sample)
     t = run(S) if S != S2 else t2
@@ -259,6 +287,12 @@ def config_block(args, cfg, X, nnz_c):
             "scale": args.scale, "step": "one HOQRI sweep (core + TTMcTC + FP64 QR per mode, fit)",
             "l2": "inputs larger than L2 (nonzero streams of every mode stay resident in HBM)",
             "parallelism": f"replicas x{args.gpus}"}
+
+
+def config_block_str(name, cfg, nnz):
+    return (f"{name}: {'x'.join(str(d) for d in cfg['dims'])}, nnz {nnz}, {cfg['dist']}"
+            f"{'(' + str(cfg.get('s')) + ')' if cfg['dist'] == 'zipf' else ''}, ranks {tuple(cfg['ranks'])}, "
+            f"{cfg['iters']} sweeps")
 
 
 def stream_roofline(X, cfg, rows, nnz, prof, prec, peaks, nsm, cfg_name):
@@ -338,43 +372,260 @@ def hosvd_init(hoqri, torch, X, U0, cfg, stream, prec, power_iters=2):
             "step": "orthogonal iteration on X_(n) X_(n)^T from the nonzeros + QR, every mode"}
 
 
-def mixed_vs_plain(hoqri, torch, X, U0, cfg, stream, steps, warmup, fit_iters=3):
-    """The split-BF16 form against the plain FP32 method on the same workload:
-    sweep throughput of both, and the relative error of the residual after
-    fit_iters sweeps from the same initial factors against the FP64 path."""
+def _ctx(hoqri, torch, X, U0, ranks, prec, stream, **opts):
+    """A context on the workload from device copies of its arrays (the inputs
+    are converted to the precision's storage type first)."""
+    import numpy as np
+    dt = np.float64 if prec == hoqri.HOQRI_FP64 else np.float32
+    idx_d = [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in X.idx]
+    vals_d = torch.from_numpy(np.ascontiguousarray(X.vals.astype(dt))).cuda()
+    U_d = [torch.from_numpy(np.ascontiguousarray(u.astype(dt))).cuda() for u in U0]
+    opt = hoqri.hoqri_default_options(prec=prec, **opts)
+    c = hoqri.hoqri_create(X.dims, ranks, X.nnz, idx_d, vals_d, opt, U_d, stream.cuda_stream)
+    del idx_d, vals_d
+    return c
+
+
+PRECS = (("fp64", 0), ("fp32", 1), ("bf16x3", 2))
+
+
+def _sample_rows(X, n, k_heavy=4, k_rand=4, seed=11):
+    """Rows of mode n for the A_n check: k_heavy rows at the 99th percentile of
+    row length (long rows, cheap enough for the oracle) and k_rand random rows."""
+    import numpy as np
+    cnt = np.bincount(X.idx[n], minlength=X.dims[n])
+    nz = np.flatnonzero(cnt)
+    order = nz[np.argsort(cnt[nz], kind="stable")]
+    q = int(0.99 * (len(order) - 1))
+    heavy = order[max(0, q - k_heavy):q]
+    rng = np.random.default_rng(seed)
+    rand = rng.choice(nz, size=min(k_rand, len(nz)), replace=False)
+    return np.unique(np.concatenate([heavy, rand])).astype(np.int32)
+
+
+def forms_leg(hoqri, torch, X, U0, cfg, stream, steps, warmup, peaks, nsm, cfg_name, orc=None):
+    """FP64, FP32 and split-BF16 on one workload from the same initial factors:
+    the residual after every one of the configuration's sweeps, the relative
+    fit error of FP32 and split-BF16 against FP64 at every sweep, the sweep
+    throughput of FP32 and split-BF16 (CUDA events, graph replay), the roofline
+    entry of their nonzero-stream kernel, and (orc) 16 sampled core entries and
+    sampled rows of A_0 at the initial factors against the oracle (rows by the
+    element-wise TTMcTC of Alg. 3, given the FP64 path's core)."""
     import numpy as np
     N = X.N
-    res = {}
-    hist = {}
-    for name, prec in (("fp64", hoqri.HOQRI_FP64), ("fp32", hoqri.HOQRI_FP32), ("bf16x3", hoqri.HOQRI_BF16X3)):
-        dt = np.float64 if prec == hoqri.HOQRI_FP64 else np.float32
-        idx_d = [torch.from_numpy(a).cuda() for a in X.idx]
-        vals_d = torch.from_numpy(X.vals.astype(dt)).cuda()
-        U_d = [torch.from_numpy(u.astype(dt)).cuda() for u in U0]
-        opt = hoqri.hoqri_default_options(prec=prec)
-        c = hoqri.hoqri_create(X.dims, cfg["ranks"], X.nnz, idx_d, vals_d, opt, U_d, stream.cuda_stream)
-        del idx_d, vals_d
-        hist[name] = hoqri.hoqri_iterate(c, fit_iters)
-        if prec != hoqri.HOQRI_FP64:
-            nnz_c, _, _ = hoqri.hoqri_info(c, N)
-            ms = timed_sweeps(hoqri, torch, c, stream, steps, warmup)
-            res[name] = {"value": nnz_c * N * steps / (ms / 1e3), "ms_per_step": ms / steps}
-        hoqri.hoqri_destroy(c)
+    iters = int(cfg["iters"])
+    ranks = cfg["ranks"]
+    P = int(np.prod(ranks))
+    rng = np.random.default_rng(5)
+    lin = np.sort(rng.choice(P, size=min(16, P), replace=False)).astype(np.int64)
+    rows = _sample_rows(X, 0)
+    res = {"workload": config_block_str(cfg_name, cfg, X.nnz), "sweeps": iters}
+    hist, G0, A0 = {}, {}, {}
+    for name, prec in PRECS:
+        c = _ctx(hoqri, torch, X, U0, ranks, prec, stream)
+        try:
+            G = torch.empty(P, dtype=torch.float64 if prec == 0 else torch.float32, device="cuda")
+            hoqri.hoqri_core(c, G)
+            A = torch.empty((X.dims[0], ranks[0]), dtype=G.dtype, device="cuda")
+            hoqri.hoqri_ttmctc(c, 0, A)
+            torch.cuda.synchronize()
+            G0[name] = G.cpu().double().numpy()
+            A0[name] = A[torch.from_numpy(rows.astype(np.int64)).cuda()].cpu().double().numpy()
+            del A
+            hist[name] = hoqri.hoqri_iterate(c, iters)
+            if prec != 0:
+                nnz_c, rws, _ = hoqri.hoqri_info(c, N)
+                ms = timed_sweeps(hoqri, torch, c, stream, steps, warmup)
+                hoqri.hoqri_profile_enable(c, True)
+                hoqri.hoqri_iterate(c, 2, want_hist=False)
+                prof, _ = hoqri.hoqri_profile_read(c)
+                hoqri.hoqri_profile_enable(c, False)
+                rf = stream_roofline(X, cfg, rws, nnz_c, prof, prec, peaks, nsm, cfg_name)
+                res[name] = {"value": nnz_c * N * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                             "roofline": {k: rf[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                             "ms_per_launch", "peak_source")}}
+        finally:
+            hoqri.hoqri_destroy(c)
+    res["resid_per_sweep"] = {k: [float(v) for v in h] for k, h in hist.items()}
     for name in ("fp32", "bf16x3"):
-        res[name]["fit_rel_err_vs_fp64"] = float(np.max(np.abs(hist[name] - hist["fp64"]) / hist["fp64"]))
-    res["fit_sweeps"] = fit_iters
+        e = np.abs(hist[name] - hist["fp64"]) / hist["fp64"]
+        res[name]["fit_rel_err_vs_fp64_per_sweep"] = [float(v) for v in e]
+        res[name]["fit_rel_err_vs_fp64_max"] = float(e.max())
+        res[name]["fit_rel_err_vs_fp64_final"] = float(e[-1])
     res["speedup_bf16x3_over_fp32"] = res["bf16x3"]["value"] / res["fp32"]["value"]
+    if orc is not None:
+        vo = np.ascontiguousarray(X.vals, dtype=np.float64)
+        U64 = [np.asarray(u, dtype=np.float64) for u in U0]
+        U32 = [np.asarray(u, dtype=np.float32).astype(np.float64) for u in U0]
+        v32 = np.asarray(X.vals, dtype=np.float32).astype(np.float64)
+        refG = {"fp64": orc.core_entries(X.idx, vo, U64, lin)}
+        refG["fp32"] = refG["bf16x3"] = orc.core_entries(X.idx, v32, U32, lin)
+        refA64 = orc.ttmctc_rows_with_core(X.dims, X.idx, vo, U64, 0, rows, G0["fp64"])
+        refA32 = orc.ttmctc_rows_with_core(X.dims, X.idx, v32, U32, 0, rows, G0["fp64"])
+        chk = {}
+        for name, _ in PRECS:
+            g = G0[name][lin]
+            ra = refA64 if name == "fp64" else refA32
+            chk[name] = {"G_entries_max_abs_err_over_max_abs_G": float(np.max(np.abs(g - refG[name])) /
+                                                                       np.max(np.abs(G0[name]))),
+                         "A0_rows_rel_frobenius_err": float(np.linalg.norm(A0[name] - ra) / np.linalg.norm(ra))}
+        res["vs_oracle_at_initial_factors"] = chk
+        res["vs_oracle_sample"] = (f"{len(lin)} core entries (oracle, entry by entry); rows {rows.tolist()} of "
+                                   f"A_0 (Alg. 3 given the FP64 path's core)")
     return res
+
+
+def _subspace(Ut, U):
+    """Largest principal angle (degrees) between span(Ut) and span(U), and the
+    distance min_Q ||U - Ut Q||_F of Sec. 5 (orthonormal U, Ut)."""
+    import numpy as np
+    s = np.linalg.svd(np.asarray(Ut, np.float64).T @ np.asarray(U, np.float64), compute_uv=False)
+    s = np.clip(s, 0.0, 1.0)
+    K = Ut.shape[1]
+    return float(np.degrees(np.arccos(s.min()))), float(np.sqrt(max(0.0, 2.0 * K - 2.0 * s.sum())))
+
+
+def planted_leg(hoqri, torch, X, U0, cfg, stream, steps, warmup):
+    """The planted-Tucker workload: FP64, FP32 and split-BF16 contexts from the
+    same initial factors for the configuration's sweeps; the residual after each
+    sweep, the fit error against FP64, sweep throughput, and the subspace angle
+    and distance of every factor to the planted one."""
+    import numpy as np
+    N = X.N
+    iters = int(cfg["iters"])
+    ranks = cfg["ranks"]
+    Ut = X.meta["U_true"]
+    res = {"workload": config_block_str("c4", cfg, X.nnz), "sweeps": iters,
+           "sampling_fraction": float(X.nnz / np.prod(np.asarray(X.dims, dtype=np.float64))),
+           "initial_subspace": [_subspace(Ut[n], U0[n]) for n in range(N)]}
+    hist = {}
+    for name, prec in PRECS:
+        c = _ctx(hoqri, torch, X, U0, ranks, prec, stream)
+        try:
+            hist[name] = hoqri.hoqri_iterate(c, iters)
+            dt = np.float64 if prec == 0 else np.float32
+            Us = []
+            for n in range(N):
+                U = np.empty((X.dims[n], ranks[n]), dtype=dt)
+                hoqri.hoqri_get_factor(c, n, U)
+                Us.append(U)
+            ent = {"resid_per_sweep": [float(v) for v in hist[name]],
+                   "subspace_angle_deg_and_distance": [_subspace(Ut[n], Us[n]) for n in range(N)]}
+            if prec != 0:
+                nnz_c, _, _ = hoqri.hoqri_info(c, N)
+                ms = timed_sweeps(hoqri, torch, c, stream, steps, warmup)
+                ent.update({"value": nnz_c * N * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps})
+            res[name] = ent
+        finally:
+            hoqri.hoqri_destroy(c)
+    for name in ("fp32", "bf16x3"):
+        e = np.abs(hist[name] - hist["fp64"]) / hist["fp64"]
+        res[name]["fit_rel_err_vs_fp64_max"] = float(e.max())
+        res[name]["fit_rel_err_vs_fp64_final"] = float(e[-1])
+    return res
+
+
+def sweeps_leg(hoqri, torch, stream, orc=None, oracle_budget_s=2.0):
+    """The synthetic experiments of Sec. 6.1 on I^N tensors with uniform indices
+    and values: per-iteration time against the dimension (Fig. 1: I = 1e2 ..
+    1e6, nnz = 10 I, rank 10^3; Fig. 6: I = 1e2 .. 3e3, nnz = 10 I and 100 I),
+    against the core rank (Fig. 7: I = 600, K = 4 .. 20) and the convergence
+    runs (N = 3, 4, 5 at I = 600, 200, 80, nnz = 10 I and 100 I, rank 10^N, at
+    most 100 sweeps or until the residual changes by less than 1e-12).  GPU
+    times are CUDA events around hoqri_iterate (FP32); the oracle's time per
+    sweep is measured where one sweep is estimated below oracle_budget_s."""
+    import numpy as np
+    from paper_2510_16930_gb300 import inputs
+    out = {}
+
+    def point(dims, ranks, nnz, seed, iters=10):
+        X = inputs.random_sparse(dims, nnz, seed, dist="uniform", values="uniform", dtype=np.float32)
+        U0 = inputs.orthonormal_factors(dims, ranks, seed + 1)
+        c = _ctx(hoqri, torch, X, U0, ranks, 1, stream)
+        try:
+            hoqri.hoqri_iterate(c, 2, want_hist=False)
+            hoqri.hoqri_synchronize(c)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            hoqri.hoqri_iterate(c, iters, want_hist=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / iters
+            r, _, _ = hoqri.hoqri_fit(c)
+        finally:
+            hoqri.hoqri_destroy(c)
+        ent = {"I": dims[0], "N": len(dims), "K": ranks[0], "nnz": int(nnz), "gpu_ms_per_iter": ms, "resid": r}
+        # oracle: one sweep of Alg. 2 costs about 2 N nnz P multiply-adds (Alg. 3 and the core)
+        if orc is not None and 2.0 * len(dims) * nnz * np.prod(ranks) / 2e9 < oracle_budget_s:
+            t0 = time.perf_counter()
+            orc.hoqri(dims, X.idx, X.vals.astype(np.float64), U0, 1)
+            ent["oracle_ms_per_iter"] = (time.perf_counter() - t0) * 1e3
+        return ent
+
+    out["fig1_dimension"] = [point((I, I, I), (10, 10, 10), 10 * I, 100 + k)
+                             for k, I in enumerate((100, 1000, 10_000, 100_000, 1_000_000))]
+    out["fig6_dimension"] = [point((I, I, I), (10, 10, 10), f * I, 200 + 3 * k + f)
+                             for k, I in enumerate((100, 300, 600, 1000, 2000, 3000)) for f in (10, 100)]
+    out["fig7_rank"] = [point((600, 600, 600), (K, K, K), f * 600, 300 + K + f)
+                        for K in (4, 8, 12, 16, 20) for f in (10, 100)]
+    conv = []
+    for N, I in ((3, 600), (4, 200), (5, 80)):
+        for f in (10, 100):
+            dims, ranks = (I,) * N, (10,) * N
+            X = inputs.random_sparse(dims, f * I, 400 + N * 10 + f, dist="uniform", values="uniform",
+                                     dtype=np.float32)
+            U0 = inputs.orthonormal_factors(dims, ranks, 401 + N * 10 + f)
+            c = _ctx(hoqri, torch, X, U0, ranks, 1, stream, tol=1e-12)
+            try:
+                t0 = time.perf_counter()
+                h = hoqri.hoqri_run(c, 100)
+                t = time.perf_counter() - t0
+                done = len(h)
+            finally:
+                hoqri.hoqri_destroy(c)
+            conv.append({"N": N, "I": I, "nnz": f * I, "K": 10, "sweeps": int(done), "seconds": t,
+                         "resid_first": float(h[0]), "resid_final": float(h[done - 1])})
+    out["convergence"] = conv
+    out["note"] = "uniform indices and values, FP32, the paper's sizes; CPU oracle timed on the host cores"
+    return out
 
 
 # ---------------------------------------------------------------------------- ours
 
+def _gen_config(name):
+    """A benchmark workload drawn in a worker process (seeded; the same arrays
+    as in the main process)."""
+    from paper_2510_16930_gb300 import inputs
+    return inputs.make_config(name)
+
+
 def run_ours(args):
     import numpy as np
+    legs = set() if args.no_mixed else {x.strip() for x in args.legs.split(",") if x.strip()}
+    if args.no_hosvd:
+        legs.discard("hosvd")
+    if args.serve_requests <= 0:
+        legs.discard("serve")
+    rank, world, local = dist_info()
+    side = rank == 0 and world == 1
+    # workloads of the later legs are drawn by a process pool while the main
+    # workload runs (spawn processes: safe to start before CUDA is initialised)
+    pool = None
+    pending = {}
+    if side and legs & {"c3", "c4", "serve"}:
+        import multiprocessing as mp
+        pool = mp.get_context("spawn").Pool(processes=max(2, min(16, (os.cpu_count() or 4) - 2)))
+        for name in ("c3", "c4"):
+            if name in legs:
+                pending[name] = pool.apply_async(_gen_config, (name,))
+        if "serve" in legs:
+            from paper_2510_16930_gb300 import serve as serve_mod
+            pending["serve"] = serve_mod.draw_requests_async(pool, args.serve_requests, serve_mod.SERVE_SEED,
+                                                             max_pm=SERVE_MAX_PM)
+
     import torch
     from paper_2510_16930_gb300 import hoqri
 
-    rank, world, local = dist_info()
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
@@ -392,7 +643,7 @@ def run_ours(args):
     vals_d = torch.from_numpy(X.vals.astype(npdt)).cuda()
     U0_d = [torch.from_numpy(u.astype(npdt)).cuda() for u in U0]
     torch.cuda.synchronize()
-    opt = hoqri.hoqri_default_options(prec=prec, chunk_nnz=args.chunk)
+    opt = hoqri.hoqri_default_options(prec=prec, chunk_nnz=args.chunk, one_stream=args.one_stream)
     ctx = hoqri.hoqri_create(X.dims, cfg["ranks"], X.nnz, idx_d, vals_d, opt, U0_d, stream.cuda_stream)
     nnz_c, rows, dev_bytes = hoqri.hoqri_info(ctx, N)
     del idx_d, vals_d
@@ -436,8 +687,8 @@ def run_ours(args):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    roofline = stream_roofline(X, cfg, rows, nnz_c, prof, prec, peaks,
-                               torch.cuda.get_device_properties(local).multi_processor_count, args.config)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    roofline = stream_roofline(X, cfg, rows, nnz_c, prof, prec, peaks, nsm, args.config)
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -446,9 +697,10 @@ def run_ours(args):
            "data": "synthetic", "config": config_block(args, cfg, X, nnz_c), "roofline": roofline,
            "gpu_launches": int(launches1 - launches0), "clocks": clk,
            "final_resid": resid_last, "device_bytes": dev_bytes}
+    hoqri.hoqri_destroy(ctx)
     # end to end through the public API from pinned host buffers (before the
-    # mixed-precision and serving legs, whose many short-lived contexts leave
-    # the device memory pool in a state that slows a following large create)
+    # other legs, whose many short-lived contexts leave the device memory pool
+    # in a state that slows a following large create)
     if not args.no_e2e:
         iters = int(cfg["iters"])
         idx_h = [torch.from_numpy(a).pin_memory() for a in X.idx]
@@ -472,32 +724,68 @@ def run_ours(args):
             torch.cuda.synchronize()
             if i > 0:
                 times.append(time.perf_counter() - t0)
-        t_e2e = max(times) if world == 1 else max(times)
+        t_e2e = max(times)
         if world > 1:
             t = torch.tensor([t_e2e], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             t_e2e = float(t.item())
         out["e2e"] = {"value": nnz_c * N * iters * world / t_e2e, "unit": UNIT, "h2d_bytes_per_step": bi,
                       "d2h_bytes_per_step": bo,
-                      "step": f"hoqri_create from pinned host COO and initial factors + {iters} sweeps + factors and fit to host",
+                      "step": f"hoqri_create from pinned host COO and initial factors + {iters} sweeps + "
+                              f"factors and fit to host",
                       "s_per_step": t_e2e}
-    if rank == 0 and world == 1 and not args.no_mixed and prec != hoqri.HOQRI_FP64:
-        out["mixed_vs_fp32"] = mixed_vs_plain(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup)
-    if rank == 0 and world == 1 and args.serve_requests > 0:
-        from paper_2510_16930_gb300 import serve
-        out["serve"] = serve.serve_benchmark(n_req=args.serve_requests)
-        out["serve"]["workload"] = ("serving mix: Poisson arrivals at 0.8 x measured capacity, order 3 (p=0.7) "
-                                    "or 4, dims U[1e3,1e6], log10 nnz ~ N(5.5,0.5) in [4,7], Zipf(1.1), ranks "
-                                    "{4,8,16,32}, 10 sweeps each, FP32; a bounded sample of the 2000-request stream")
-    if rank == 0 and world == 1 and not args.no_hosvd:
+        del idx_h, vals_h, U0_h, U_h
+    orc = None
+    if side and legs & {"forms", "c3", "sweeps"}:
+        from oracle import oracle as orc
+        orc.build()
+    leg_s = {}
+
+    def leg(name, fn):
+        t0 = time.perf_counter()
         try:
-            out["init_hosvd"] = hosvd_init(hoqri, torch, X, U0, cfg, stream, prec)
+            out[name] = fn()
         except Exception as e:  # reported, never fatal to the bench line
-            out["init_hosvd"] = {"error": str(e)}
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        leg_s[name] = time.perf_counter() - t0
 
-    hoqri.hoqri_destroy(ctx)
+    if side and "forms" in legs and prec != hoqri.HOQRI_FP64:
+        leg("forms", lambda: forms_leg(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup, peaks, nsm,
+                                       args.config, orc))
+    if side and "hosvd" in legs:
+        leg("init_hosvd", lambda: hosvd_init(hoqri, torch, X, U0, cfg, stream, prec))
+    if side and "c3" in legs:
+        def c3():
+            X3, U3, cfg3 = pending["c3"].get()
+            try:
+                return forms_leg(hoqri, torch, X3, U3, cfg3, stream, max(3, args.steps // 4), args.warmup, peaks,
+                                 nsm, "c3", orc)
+            finally:
+                del X3
+        leg("c3", c3)
+    if side and "c4" in legs:
+        def c4():
+            X4, U4, cfg4 = pending["c4"].get()
+            return planted_leg(hoqri, torch, X4, U4, cfg4, stream, max(3, args.steps // 4), args.warmup)
+        leg("c4", c4)
+    if side and "sweeps" in legs:
+        leg("sweeps", lambda: sweeps_leg(hoqri, torch, stream, orc))
+    if side and "serve" in legs:
+        def srv():
+            from paper_2510_16930_gb300 import serve as serve_mod
+            reqs = pending["serve"]()
+            r = serve_mod.serve_benchmark(reqs=reqs)
+            r["workload"] = ("c5 serving mix: Poisson arrivals at 0.8 x the measured capacity, order 3 (p=0.7) "
+                             "or 4, dims U[1e3,1e6], log10 nnz ~ N(5.5,0.5) in [4,7], Zipf(1.1), ranks from "
+                             "{4,8,16,32} redrawn while some P_{-n} > 2048, 10 sweeps each, FP32")
+            return r
+        leg("serve", srv)
+    if pool is not None:
+        pool.terminate()
+    if leg_s:
+        out["leg_seconds"] = leg_s
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if side and not args.no_cpu_baseline:
         rate, cores, sample, secs = cpu_oracle_rate(X, U0, args.cpu_seconds)
         out["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                                "seconds": secs}

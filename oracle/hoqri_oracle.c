@@ -260,6 +260,20 @@ void hoqri_oracle_ttmctc_rows(int N, const int64_t *dims, const int32_t *ranks, 
     if (!G_out) free(G);
 }
 
+/* Selected rows of A_n (Alg. 3 restricted to i_n in rows[]) with a core G
+ * supplied by the caller (P entries, the layout above) instead of computed
+ * here: the element-wise TTMcTC step of Alg. 3 alone.  out is nr x K_n. */
+void hoqri_oracle_ttmctc_rows_with_core(int N, const int64_t *dims, const int32_t *ranks, int64_t nnz,
+                                        const int32_t *const *idx, const double *vals,
+                                        const double *const *U, int n, const double *G, int64_t nr,
+                                        const int32_t *rows, double *out) {
+    int64_t *start, *list;
+    mode_index_sets(dims[n], nnz, idx[n], &start, &list);
+    ttmctc_rows_given_core(N, ranks, nnz, idx, vals, U, n, G, start, list, nr, rows, out);
+    free(start);
+    free(list);
+}
+
 /* ----------------------------------------------------- TTMcTC, matrix version */
 
 /*

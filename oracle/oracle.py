@@ -62,6 +62,9 @@ def lib():
         L.hoqri_oracle_ttmctc_rows.restype = None
         L.hoqri_oracle_ttmctc_rows.argtypes = [C.c_int, _i64p, _i32p, C.c_int64, C.POINTER(_i32p), _f64p,
                                                C.POINTER(_f64p), C.c_int, C.c_int64, _i32p, _f64p, _f64p]
+        L.hoqri_oracle_ttmctc_rows_with_core.restype = None
+        L.hoqri_oracle_ttmctc_rows_with_core.argtypes = [C.c_int, _i64p, _i32p, C.c_int64, C.POINTER(_i32p), _f64p,
+                                                         C.POINTER(_f64p), C.c_int, _f64p, C.c_int64, _i32p, _f64p]
         L.hoqri_oracle_ttmctc_matrix.restype = None
         L.hoqri_oracle_ttmctc_matrix.argtypes = [C.c_int, _i64p, _i32p, C.c_int64, C.POINTER(_i32p), _f64p,
                                                  C.POINTER(_f64p), C.c_int, _f64p]
@@ -173,6 +176,23 @@ def ttmctc_rows(dims, idx, vals, U, n, rows, return_core=False):
                                    M.arr, int(n), rows.shape[0], _p(rows, _i32p), _p(out, _f64p), _p(G, _f64p))
     if return_core:
         return out, G.reshape(tuple(int(k) for k in r))
+    return out
+
+
+def ttmctc_rows_with_core(dims, idx, vals, U, n, rows, G):
+    """Rows `rows` of A_n by the element-wise step of Alg. 3, with the core G
+    given (for sizes where the oracle's own core, O(nnz P N), is too slow: G is
+    then checked separately at sampled entries with core_entries)."""
+    c, M = _Coo(idx, vals), _Mats(U)
+    d, r = _dims(dims), _ranks(M.m)
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    Gd = np.ascontiguousarray(np.asarray(G, dtype=np.float64).ravel())
+    if Gd.shape[0] != int(np.prod(r)):
+        raise ValueError("G has the wrong number of entries")
+    out = np.empty((rows.shape[0], int(r[n])), dtype=np.float64)
+    lib().hoqri_oracle_ttmctc_rows_with_core(c.N, _p(d, _i64p), _p(r, _i32p), c.nnz, c.idx_arr, _p(c.vals, _f64p),
+                                             M.arr, int(n), _p(Gd, _f64p), rows.shape[0], _p(rows, _i32p),
+                                             _p(out, _f64p))
     return out
 
 

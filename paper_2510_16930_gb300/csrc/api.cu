@@ -216,8 +216,13 @@ static hoqri_status check_mode(hoqri_ctx *c, int32_t mode) {
     return HOQRI_OK;
 }
 
-// G <- X x {U^T} with the current factors, computed from mode m's stream.
+// G <- X x {U^T} with the current factors, computed from mode m's stream.  A
+// mode on the two-pass kernels computes it from the context's core_mode
+// instead: every mode's stream gives the same G (Alg. 3), and the row-grouped
+// cost nnz P_{-m} + R_m P (Table 2) differs between modes (R_m P dominates for
+// large cores and many short rows).
 static hoqri_status refresh_core(hoqri_ctx *c, int m, double *slot) {
+    if (!hyb_mode(c, m) && c->core_mode >= 0) m = c->core_mode;
     if (hyb_mode(c, m)) {
         cudaEvent_t e0 = nullptr;
         HQ_TRY(prof_begin(c, 0, &e0));
@@ -309,6 +314,14 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
         if ((int64_t)ranks[n] > dims[n] || (int64_t)ranks[n] > pm) {
             set_error("hoqri_create: K_n must not exceed I_n nor prod_{m != n} K_m");
             return HOQRI_ERR_RANK;
+        }
+    }
+    {
+        int64_t P = 1;
+        for (int n = 0; n < N; ++n) P *= ranks[n];
+        if (P > ((int64_t)1 << 26)) {
+            set_error("hoqri_create: prod K_n above 2^26 core entries is not supported");
+            return HOQRI_ERR_UNSUPPORTED;
         }
     }
     hoqri_options o;
@@ -412,6 +425,18 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
     if ((s = dalloc(c, &c->A, maxIK * c->rsize)) != HOQRI_OK) return fail(s);
     if ((s = qr_init(c)) != HOQRI_OK) return fail(s);
     if ((s = passes_init(c)) != HOQRI_OK) return fail(s);
+    {
+        // the two-pass core is computed from the mode of least nnz P_{-m} + R_m P
+        double best = 0.0;
+        for (int m = 0; m < N; ++m) {
+            if (hyb_mode(c, m)) continue;
+            const double cost = (double)c->nnz * (double)(c->P / c->K[m]) + (double)c->ms[m].R * (double)c->P;
+            if (c->core_mode < 0 || cost < best) {
+                best = cost;
+                c->core_mode = m;
+            }
+        }
+    }
     if (U0) {
         for (int n = 0; n < N; ++n) {
             if (!U0[n]) {

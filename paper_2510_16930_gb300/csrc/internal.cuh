@@ -163,6 +163,7 @@ struct hoqri_ctx {
     float *fpart = nullptr;             // [W][2][P_{-n}] rows cut by the fiber pass's ranges
     int64_t fpart_bytes = 0;
     int core_grid = 0;                  // CTAs of the core pass (fixed per context)
+    int core_mode = -1;                 // stream the two-pass core is computed from (cheapest)
     int pass_grid = 0;
     int core_grid_fast = 0;             // the same for the register-tiled FP32 kernels
     int pass_grid_fast = 0;

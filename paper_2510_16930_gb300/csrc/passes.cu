@@ -113,6 +113,10 @@ struct PassArgs {
     int Pm;                        // prod Ko = P_{-n}
     int Kl;                        // Ko[nm1-1] (last other mode: fastest in y)
     int L;                         // Pm / Kl
+    // column block of this launch: columns [e0, e0 + Pb) of Y_(n) and G_(n)
+    // (e0 and Pb multiples of Kl; one block covers every column when Pm <= 2048)
+    int e0, Pb, q0, Lb;            // q0 = e0 / Kl, Lb = Pb / Kl Kronecker prefixes
+    int accum;                     // TTMcTC: add into A / apart (blocks after the first)
     const int32_t *oidx[HOQRI_MAXN - 1];
     const T *Uo[HOQRI_MAXN - 1];
     const T *Un;
@@ -132,10 +136,14 @@ struct PassArgs {
     T *cpart;                      // core: [grid][Kn*Pm]
 };
 
-// Generic pass: y lives in registers (element e = lane + 32*j of the lane);
-// each nonzero's factor rows are staged in the warp's shared row buffer, the
-// Kronecker prefix z (all other modes but the last) is formed once per nonzero
-// in shared memory, and y[e] += z[e / Kl] * u_last[e % Kl].
+// Generic pass: y lives in registers (element e = e0 + lane + 32*j of the
+// lane, over the launch's column block); each nonzero's factor rows are staged
+// in the warp's shared row buffer, the block's Kronecker prefixes z (all other
+// modes but the last) are formed once per nonzero in shared memory, and
+// y[e] += z[e / Kl] * u_last[e % Kl].  P_{-n} above 2048 runs as several
+// launches, one per column block: the core pass fills its block's columns of
+// the CTA partials, the TTMcTC pass adds its block's share of A_n(i, :) =
+// G_(n) y_i in block order.
 template <typename T, int PL, bool CORE>
 __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -152,18 +160,19 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     }
     T *rowbuf = wbase + (size_t)wib * a.wstride;
     T *zbuf = rowbuf + a.rtot;
+    const int KnPb = a.Kn * a.Pb;
     T *acc = nullptr;
     if (CORE) {
-        acc = a.acc_in_smem ? zbuf + a.L : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + wib) * KnPm;
-        for (int p = lane; p < KnPm; p += 32) acc[p] = T(0);
+        acc = a.acc_in_smem ? zbuf + a.Lb : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + wib) * KnPb;
+        for (int p = lane; p < KnPb; p += 32) acc[p] = T(0);
     }
     __syncthreads();
 
-    int qj[PL], rj[PL];
+    int qj[PL], rj[PL];  // prefix (relative to the block's first) and last-mode index of column e
 #pragma unroll
     for (int j = 0; j < PL; ++j) {
-        int e = lane + 32 * j;
-        qj[j] = e / a.Kl;
+        int e = a.e0 + lane + 32 * j;
+        qj[j] = e / a.Kl - a.q0;
         rj[j] = e % a.Kl;
     }
     const int lastoff = a.roff[a.nm1 - 1];
@@ -199,9 +208,9 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
                         for (int k = lane; k < a.Ko[j]; k += 32) rowbuf[a.roff[j] + k] = src[k];
                     }
                     __syncwarp();
-                    for (int l = lane; l < a.L; l += 32) {
+                    for (int l = lane; l < a.Lb; l += 32) {
                         T z = x;
-                        int rem = l;
+                        int rem = a.q0 + l;
                         for (int j = a.nm1 - 2; j >= 0; --j) {
                             const int k = rem % a.Ko[j];
                             rem /= a.Ko[j];
@@ -212,7 +221,7 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
                     __syncwarp();
 #pragma unroll
                     for (int j = 0; j < PL; ++j)
-                        if (lane + 32 * j < a.Pm) y[j] += zbuf[qj[j]] * rowbuf[lastoff + rj[j]];
+                        if (lane + 32 * j < a.Pb) y[j] += zbuf[qj[j]] * rowbuf[lastoff + rj[j]];
                     __syncwarp();
                 }
             }
@@ -220,26 +229,26 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
             if (CORE) {
                 for (int kn = 0; kn < a.Kn; ++kn) {
                     const T u = a.Un[(int64_t)row * a.Kn + kn];
-                    T *ak = acc + (size_t)kn * a.Pm;
+                    T *ak = acc + (size_t)kn * a.Pb;
 #pragma unroll
                     for (int j = 0; j < PL; ++j) {
                         const int e = lane + 32 * j;
-                        if (e < a.Pm) ak[e] += u * y[j];
+                        if (e < a.Pb) ak[e] += u * y[j];
                     }
                 }
             } else {
                 const bool full = (rs >= s0) && (re <= s1);
                 T *dst = full ? a.A + (int64_t)row * a.Kn : a.apart + ch * a.Kn;
                 for (int kn = 0; kn < a.Kn; ++kn) {
-                    const T *g = gn + (size_t)kn * a.Pm;
+                    const T *g = gn + (size_t)kn * a.Pm + a.e0;
                     T s = T(0);
 #pragma unroll
                     for (int j = 0; j < PL; ++j) {
                         const int e = lane + 32 * j;
-                        if (e < a.Pm) s += g[e] * y[j];
+                        if (e < a.Pb) s += g[e] * y[j];
                     }
                     s = warp_allsum(s);
-                    if (lane == 0) dst[kn] = s;
+                    if (lane == 0) dst[kn] = a.accum ? dst[kn] + s : s;
                 }
             }
             pos = a1;
@@ -248,15 +257,16 @@ __global__ void __launch_bounds__(GEN_WARPS * 32) k_pass_generic(PassArgs<T> a) 
     }
     if (CORE) {
         __syncthreads();
-        // CTA partial = sum of the warp accumulators in warp order
-        for (int p = threadIdx.x; p < KnPm; p += blockDim.x) {
+        // CTA partial = sum of the warp accumulators in warp order (the block's columns)
+        for (int p = threadIdx.x; p < KnPb; p += blockDim.x) {
             T s = T(0);
             for (int w = 0; w < GEN_WARPS; ++w) {
-                const T *aw = a.acc_in_smem ? (wbase + (size_t)w * a.wstride + a.rtot + a.L)
-                                            : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + w) * KnPm;
+                const T *aw = a.acc_in_smem ? (wbase + (size_t)w * a.wstride + a.rtot + a.Lb)
+                                            : a.acc_glob + ((size_t)blockIdx.x * GEN_WARPS + w) * KnPb;
                 s += aw[p];
             }
-            a.cpart[(size_t)blockIdx.x * KnPm + p] = s;
+            const int kn = p / a.Pb, e = p - kn * a.Pb;
+            a.cpart[(size_t)blockIdx.x * KnPm + (size_t)kn * a.Pm + a.e0 + e] = s;
         }
     }
 }
@@ -557,9 +567,8 @@ __global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nbl
         for (int q = 0; q < nw; ++q) t += sh[q][lane];
         double sq = 0.0;
         if (p < P) {
-            const T v = (T)t;
-            G[rowmajor_of(m, p)] = v;
-            sq = (double)v * (double)v;
+            G[rowmajor_of(m, p)] = (T)t;
+            sq = t * t;  // the FP64 sum, before the entry is rounded to T
         }
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) gpart[blockIdx.x] = sq;
@@ -612,6 +621,23 @@ int pl_for(int Pm) {
     int pl = 1;
     while (32 * pl < Pm) pl <<= 1;
     return pl;
+}
+
+// columns of Y_(n) per launch of the generic pass: all of them up to 2048,
+// else the largest multiple of K_l (the last other mode's rank) not above 2048
+int gen_block(int Pm, int Kl) { return Pm <= 2048 ? Pm : (2048 / Kl) * Kl; }
+
+// columns per launch of the generic core pass: as gen_block, but narrower where
+// the warps' K_n x Pb accumulators would not fit in shared memory (a multiple of
+// K_l), so the accumulators never live in global memory: a row's rank-1 update
+// of the core is K_n x P_{-n} read-modify-writes, far too many for global memory
+int gen_block_core(int Pm, int Kl, int Kn, int rtot, size_t rsize) {
+    int Pb = gen_block(Pm, Kl);
+    auto fits = [&](int pb) {
+        return (size_t)GEN_WARPS * (size_t)(rtot + pb / Kl + Kn * pb + 3) * rsize <= SMEM_CAP;
+    };
+    while (Pb > Kl && !fits(Pb)) Pb = std::max(Kl, ((Pb / 2) / Kl) * Kl);
+    return Pb;
 }
 
 // ---- fast-path plan for mode n
@@ -679,8 +705,15 @@ void fill_common(hoqri_ctx *c, int n, PassArgs<T> &a) {
 }
 
 template <typename T, bool CORE>
-hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem) {
-    const int pl = pl_for(a.Pm);
+hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem, int Pblk) {
+    // one launch per column block of Pblk columns (in block order: the TTMcTC pass adds into A)
+    for (int e0 = 0; e0 < a.Pm; e0 += Pblk) {
+        a.e0 = e0;
+        a.Pb = std::min(Pblk, a.Pm - e0);
+        a.q0 = e0 / a.Kl;
+        a.Lb = a.Pb / a.Kl;
+        a.accum = e0 > 0;
+        const int pl = pl_for(a.Pb);
 #define HQ_GEN(PLV)                                                                                   \
     case PLV: {                                                                                       \
         auto kern = k_pass_generic<T, PLV, CORE>;                                                     \
@@ -689,19 +722,20 @@ hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem)
         c->nlaunch++;                                                                                 \
         break;                                                                                        \
     }
-    switch (pl) {
-        HQ_GEN(1)
-        HQ_GEN(2)
-        HQ_GEN(4)
-        HQ_GEN(8)
-        HQ_GEN(16)
-        HQ_GEN(32)
-        HQ_GEN(64)
-        default:
-            set_error("P_{-n} = prod_{m != n} K_m above 2048 is not supported by the library's kernels");
-            return HOQRI_ERR_UNSUPPORTED;
-    }
+        switch (pl) {
+            HQ_GEN(1)
+            HQ_GEN(2)
+            HQ_GEN(4)
+            HQ_GEN(8)
+            HQ_GEN(16)
+            HQ_GEN(32)
+            HQ_GEN(64)
+            default:
+                set_error("generic pass: column block above 2048 (internal)");
+                return HOQRI_ERR_UNSUPPORTED;
+        }
 #undef HQ_GEN
+    }
     HQ_CUDA(cudaGetLastError());
     return HOQRI_OK;
 }
@@ -820,20 +854,21 @@ hoqri_status core_pass_t(hoqri_ctx *c, int n, void *G_out, double *normG2_slot) 
     if (std::is_same<T, float>::value && use_fast(c, n, true, &fp)) {
         HQ_TRY(launch_fast<true>(c, n, fp, nullptr, nullptr, &grid));
     } else {
-        a.wstride = (a.rtot + a.L + KnPm + 3) & ~3;
+        const int Pb = gen_block_core(a.Pm, a.Kl, a.Kn, a.rtot, sizeof(T)), Lb = Pb / a.Kl;
+        a.wstride = (a.rtot + Lb + a.Kn * Pb + 3) & ~3;
         size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
         a.acc_in_smem = smem <= SMEM_CAP;
         if (!a.acc_in_smem) {
-            a.wstride = (a.rtot + a.L + 3) & ~3;
+            a.wstride = (a.rtot + Lb + 3) & ~3;
             smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
         }
         a.acc_glob = (T *)c->a_part;  // only used when the accumulator does not fit in smem
         a.cpart = (T *)c->core_part;
-        if (!a.acc_in_smem && (int64_t)grid * GEN_WARPS * KnPm * (int64_t)sizeof(T) > c->a_part_bytes) {
+        if (!a.acc_in_smem && (int64_t)grid * GEN_WARPS * a.Kn * Pb * (int64_t)sizeof(T) > c->a_part_bytes) {
             set_error("core pass: accumulator workspace too small");
             return HOQRI_ERR_UNSUPPORTED;
         }
-        HQ_TRY((launch_generic<T, true>(c, a, grid, smem)));
+        HQ_TRY((launch_generic<T, true>(c, a, grid, smem, Pb)));
     }
     CoreMap m = core_map(c, n);
     const int rb = (KnPm + 31) / 32;
@@ -867,11 +902,12 @@ hoqri_status ttmctc_pass_t(hoqri_ctx *c, int n, const void *G, void *A_out) {
         a.Gn = Gn;
         a.A = (T *)A_out;
         a.apart = (T *)c->a_part;
-        a.wstride = (a.rtot + a.L + 3) & ~3;
+        const int Pb = gen_block(a.Pm, a.Kl);
+        a.wstride = (a.rtot + Pb / a.Kl + 3) & ~3;
         size_t smem = (size_t)GEN_WARPS * a.wstride * sizeof(T);
-        a.gn_in_smem = (smem + (size_t)KnPm * sizeof(T)) <= SMEM_CAP;
+        a.gn_in_smem = Pb == a.Pm && (smem + (size_t)KnPm * sizeof(T)) <= SMEM_CAP;
         if (a.gn_in_smem) smem += (size_t)KnPm * sizeof(T);
-        HQ_TRY((launch_generic<T, false>(c, a, c->pass_grid, smem)));
+        HQ_TRY((launch_generic<T, false>(c, a, c->pass_grid, smem, Pb)));
     }
     if (M.nbig > 0) {
         k_fixup<T><<<(unsigned)M.nbig, 128, 0, c->stream>>>(M.big, M.row_id, (const T *)c->a_part, a.Kn, (T *)A_out);
@@ -938,7 +974,9 @@ hoqri_status passes_init(hoqri_ctx *c) {
     }
     const int64_t want = ceil_div(std::max<int64_t>(max_chunks, 1), GEN_WARPS);
     c->pass_grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)c->num_sms * 4));
-    c->core_grid = c->pass_grid;
+    // the core partials hold one copy of G per CTA: at most 256 MB of them
+    c->core_grid = (int)std::max<int64_t>(
+        1, std::min<int64_t>(c->pass_grid, ((int64_t)256 << 20) / (c->P * (int64_t)c->rsize)));
     // the register-tiled kernels run at most FAST_MAX_CTAS_PER_SM resident CTAs per SM
     c->core_grid_fast = c->num_sms * FAST_MAX_CTAS_PER_SM;
     c->pass_grid_fast = c->core_grid_fast;
@@ -959,9 +997,10 @@ hoqri_status passes_init(hoqri_ctx *c) {
                 Pm *= c->K[m];
             }
         const int64_t Kl = c->K[n == c->N - 1 ? c->N - 2 : c->N - 1];
-        const int64_t wst = (rtot + Pm / Kl + c->P + 3) & ~3LL;
+        const int64_t Pb = gen_block_core((int)Pm, (int)Kl, c->K[n], (int)rtot, c->rsize);
+        const int64_t wst = (rtot + Pb / Kl + c->K[n] * Pb + 3) & ~3LL;
         if ((int64_t)GEN_WARPS * wst * (int64_t)c->rsize > (int64_t)SMEM_CAP)
-            ab = std::max(ab, (int64_t)c->core_grid * GEN_WARPS * c->P * (int64_t)c->rsize);
+            ab = std::max(ab, (int64_t)c->core_grid * GEN_WARPS * c->K[n] * Pb * (int64_t)c->rsize);
     }
     // hybrid layout + dense Y for the FP32 modes with a register-tile plan
     int64_t ybytes = 0, ypb = 0;

@@ -191,14 +191,19 @@ def planted_tucker(dims, ranks, nnz: int, sigma: float, seed: int, dtype=np.floa
     pos = random_sparse(dims, nnz, seed, dist="uniform", values="uniform", distinct=True)
     Ut = orthonormal_factors(dims, ranks, seed ^ 0x5A5A)
     Gt = _rng(seed, _P_CORE).standard_normal(tuple(ranks))
-    # ground-truth model value at each observed position (data synthesis only)
+    # ground-truth model value at each observed position (data synthesis only):
+    # the core contracted with the last mode's rows by a matrix product, then a
+    # row-wise dot with the Khatri-Rao product of the other modes' rows
     vals = np.empty(nnz, dtype=np.float64)
-    letters = "abcdefgh"[:N]
-    spec = letters + "," + ",".join("z" + l for l in letters) + "->z"
-    B = 1 << 18
+    GflatT = np.ascontiguousarray(Gt.reshape(-1, ranks[-1]).T)
+    B = 1 << 16
     for s0 in range(0, nnz, B):
-        rows = [Ut[m][pos.idx[m][s0:s0 + B]] for m in range(N)]
-        vals[s0:s0 + B] = np.einsum(spec, Gt, *rows, optimize=True)
+        rows = [np.take(Ut[m], pos.idx[m][s0:s0 + B], axis=0) for m in range(N)]
+        W = rows[-1] @ GflatT
+        kr = rows[0]
+        for m in range(1, N - 1):
+            kr = (kr[:, :, None] * rows[m][:, None, :]).reshape(kr.shape[0], -1)
+        vals[s0:s0 + B] = np.einsum("zp,zp->z", kr, W)
     scale = 1.0 / math.sqrt(float(np.mean(vals * vals)))
     noise = np.empty(nnz, dtype=np.float64)
 
@@ -223,11 +228,11 @@ class ServeRequest:
 
 def serving_mix(n_req: int, rate_hz: float, seed: int, dim_range=(1_000, 1_000_000),
                 log_nnz=(5.5, 0.5, 4.0, 7.0), rank_set=(4, 8, 16, 32),
-                p_order3: float = 0.7, max_pm: int = 2048) -> list:
+                p_order3: float = 0.7, max_pm=None) -> list:
     """Poisson arrivals of decomposition requests (order 3 w.p. p_order3 else 4).
 
-    Ranks are redrawn per request until K_n <= I_n, K_n <= prod_{m!=n} K_m and
-    prod_{m!=n} K_m <= max_pm (the largest Kronecker row the passes support)."""
+    Ranks are redrawn per request until K_n <= I_n and K_n <= prod_{m!=n} K_m
+    (and prod_{m!=n} K_m <= max_pm when max_pm is given)."""
     r = _rng(seed, _P_MIX)
     ra = _rng(seed, _P_ARR)
     t = 0.0
@@ -240,8 +245,8 @@ def serving_mix(n_req: int, rate_hz: float, seed: int, dim_range=(1_000, 1_000_0
         nnz = int(round(10 ** float(np.clip(r.normal(mu, sd), lo, hi))))
         while True:
             ranks = tuple(int(v) for v in r.choice(rank_set, size=N))
-            if all(ranks[n] <= dims[n] and ranks[n] <= math.prod(ranks[:n] + ranks[n + 1:]) <= max_pm
-                   for n in range(N)):
+            if all(ranks[n] <= dims[n] and ranks[n] <= math.prod(ranks[:n] + ranks[n + 1:]) and
+                   (max_pm is None or math.prod(ranks[:n] + ranks[n + 1:]) <= max_pm) for n in range(N)):
                 break
         out.append(ServeRequest(q, t, dims, ranks, nnz, (seed * 1000003 + q) & 0x7FFFFFFF))
     return out

@@ -85,6 +85,33 @@ def test_o_ik_form_matches_oracle(orc, shape, chunk):
         assert dev_bytes <= c1.info()[2]
 
 
+BLOCKED = [
+    # P_{-n} above 2048: the generic pass runs one launch per column block
+    ((40, 30, 20, 20), (16, 16, 16, 8), 3000, "zipf"),          # mode 3: 4096 = 2 blocks
+    ((14, 13, 12, 11, 10), (10, 10, 10, 10, 10), 2000, "uniform"),  # 10^4 = 4 blocks of 2040 + 1840
+]
+
+
+@pytest.mark.parametrize("prec", [FP64, FP32])
+@pytest.mark.parametrize("shape", BLOCKED, ids=[str(s[0]) for s in BLOCKED])
+def test_column_blocked_passes_match_oracle(orc, shape, prec):
+    dims, ranks, nnz, dist = shape
+    X, U0 = _case(dims, ranks, nnz, 4321 + nnz, dist=dist)
+    npdt = np.float64 if prec == FP64 else np.float32
+    vals = X.vals.astype(npdt)
+    U0c = [u.astype(npdt) for u in U0]
+    U0o = [u.astype(np.float64) for u in U0c]
+    vo = vals.astype(np.float64)
+    with Ctx(dims, X.idx, vals, U0c, prec, chunk=32) as c:
+        for n in range(len(dims)):
+            A_ref, G_ref = orc.ttmctc(dims, X.idx, vo, U0o, n, return_core=True)
+            A = c.ttmctc(n)
+            assert rel(A, A_ref) <= TOL[prec], (n, rel(A, A_ref))
+        assert rel(c.core(), G_ref) <= TOL[prec]
+        h = c.iterate(2)
+        assert np.all(np.isfinite(h)) and h[1] <= h[0] * (1 + 1e-12)
+
+
 def test_fit_and_nnz_after_coalescing(orc):
     dims, ranks = (50, 40, 30), (4, 4, 3)
     X, U0 = _case(dims, ranks, 6000, 77)

@@ -138,3 +138,52 @@ def test_failed_request_does_not_stop_the_others():
         assert hoqri.hoqri_server_take(srv, good) > 0
     finally:
         hoqri.hoqri_server_destroy(srv)
+
+
+def test_served_results_match_the_oracle():
+    """Small FP64 requests of order 3 and 4 served together: each request's
+    residual history end and its factors' subspaces equal the oracle's Alg. 2
+    from the same initial factors (those the library draws from the request's
+    seed, read from a lone context before any sweep)."""
+    torch = pytest.importorskip("torch")
+    from oracle import oracle as orc
+    orc.build()
+    FP64 = hoqri.HOQRI_FP64
+    cases = [((40, 30, 20), (4, 3, 5), 3000, 31), ((16, 14, 12, 10), (3, 2, 4, 2), 2500, 32),
+             ((60, 50, 40), (8, 8, 4), 5000, 33)]
+    reqs = []
+    for k, (dims, ranks, nnz, seed) in enumerate(cases):
+        X = inputs.random_sparse(dims, nnz, 1100 + k, dist="zipf", s=1.1, values="uniform", dtype=np.float64)
+        reqs.append((X, ranks, seed))
+    iters = 5
+    srv = hoqri.hoqri_server_create(8 << 30, 4)
+    try:
+        ids = [hoqri.hoqri_server_submit(srv, X.dims, ranks, X.nnz, X.idx, X.vals, iters, FP64, seed)
+               for X, ranks, seed in reqs]
+        res = {}
+        while len(res) < len(ids):
+            hoqri.hoqri_server_step(srv)
+            for k, rid in enumerate(ids):
+                if k not in res and hoqri.hoqri_server_poll(srv, rid)[0] == hoqri.HOQRI_REQ_DONE:
+                    X, ranks, _ = reqs[k]
+                    U = [np.zeros((d, r), np.float64) for d, r in zip(X.dims, ranks)]
+                    res[k] = (U, hoqri.hoqri_server_take(srv, rid, U))
+    finally:
+        hoqri.hoqri_server_destroy(srv)
+    for k, (X, ranks, seed) in enumerate(reqs):
+        # the initial factors of the request: a lone context from the same seed
+        opt = hoqri.hoqri_default_options(prec=FP64, seed=seed)
+        c = hoqri.hoqri_create(X.dims, ranks, X.nnz, X.idx, X.vals, opt, None, 0)
+        try:
+            U0 = []
+            for n, (d, r) in enumerate(zip(X.dims, ranks)):
+                u = np.zeros((d, r), np.float64)
+                hoqri.hoqri_get_factor(c, n, u)
+                U0.append(u)
+        finally:
+            hoqri.hoqri_destroy(c)
+        ref = orc.hoqri(X.dims, X.idx, X.vals, U0, iters)
+        U, r = res[k]
+        assert abs(r - ref["resid"][-1]) <= 1e-10 * ref["resid"][-1], k
+        for a, b in zip(U, ref["U"]):
+            assert np.linalg.norm(a @ a.T - b @ b.T) <= 1e-8, k

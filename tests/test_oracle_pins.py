@@ -409,3 +409,30 @@ def test_generator_is_seeded_and_shaped():
     Xd = inputs.random_sparse((50, 40, 30), 5000, 99, dist="zipf", s=1.1, distinct=True)
     keys = np.ravel_multi_index(tuple(a.astype(np.int64) for a in Xd.idx), Xd.dims)
     assert np.unique(keys).size == 5000
+
+
+def test_rows_with_a_given_core_equal_the_rows_with_the_oracle_core(orc):
+    """ttmctc_rows_with_core (the element-wise step of Alg. 3 with G supplied)
+    given the oracle's own core equals ttmctc_rows, and both equal the dense
+    matricised product X_(n) (kron of the other factors) G_(n)^T on those rows."""
+    rng = np.random.default_rng(3)
+    dims, ranks = (9, 8, 7, 6), (3, 2, 4, 2)
+    nnz = 400
+    idx = [rng.integers(0, d, nnz).astype(np.int32) for d in dims]
+    vals = rng.standard_normal(nnz)
+    U = [rng.standard_normal((d, k)) for d, k in zip(dims, ranks)]
+    for n in range(4):
+        rows = np.array([0, 3, 5], dtype=np.int32)
+        A1, G = orc.ttmctc_rows(dims, idx, vals, U, n, rows, return_core=True)
+        A2 = orc.ttmctc_rows_with_core(dims, idx, vals, U, n, rows, G)
+        assert np.array_equal(A1, A2)
+        Xd = np.zeros(dims)
+        np.add.at(Xd, tuple(idx), vals)
+        Gd = np.einsum("ijkl,ip,jq,kr,ls->pqrs", Xd, *U)  # G = X x {U^T}
+        others = [m for m in range(4) if m != n]
+        Xn = np.moveaxis(Xd, n, 0).reshape(dims[n], -1)
+        Kr = U[others[0]]
+        for m in others[1:]:
+            Kr = np.kron(Kr, U[m])
+        Gn = np.moveaxis(Gd, n, 0).reshape(ranks[n], -1)
+        assert np.allclose(A2, (Xn @ Kr @ Gn.T)[rows], rtol=1e-12, atol=1e-12)
