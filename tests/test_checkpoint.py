@@ -15,10 +15,14 @@ def test_round_trip(tmp_path, dt):
     U = [rng.standard_normal((I, K)).astype(dt) for I, K in zip(dims, ranks)]
     p = tmp_path / "ck.npz"
     prec = FP64 if dt == np.float64 else FP32
-    checkpoint.save(p, U, dims=dims, ranks=ranks, prec=prec, sweeps=7, resid_hist=[0.9, 0.8], seed=11)
+    opt = hoqri.hoqri_default_options(qr_kind=2, chunk_nnz=96, autotune=1, one_stream=3, tol=1e-9)
+    checkpoint.save(p, U, dims=dims, ranks=ranks, prec=prec, sweeps=7, resid_hist=[0.9, 0.8], seed=11, options=opt)
     ck = checkpoint.load(p)
     assert ck["dims"] == list(dims) and ck["ranks"] == list(ranks)
     assert ck["prec"] == prec and ck["sweeps"] == 7 and ck["seed"] == 11
+    o = ck["options"]
+    assert (o["prec"], o["qr_kind"], o["chunk_nnz"], o["autotune"], o["one_stream"], o["seed"]) == (prec, 2, 96, 1, 3, 11)
+    assert o["tol"] == 1e-9 and o["use_graphs"] == opt.use_graphs
     assert np.array_equal(ck["resid_hist"], [0.9, 0.8])
     for a, b in zip(U, ck["U"]):
         assert a.dtype == b.dtype and np.array_equal(a, b)
