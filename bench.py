@@ -21,6 +21,8 @@ object per further leg (each can be skipped with --legs):
   serve    the serving stream (Poisson arrivals of the request mix) through
            the request server against the same requests run one after another
            as plain contexts;
+  autotune the autotuner (lane tile, long-row threshold, work-item size) against
+           the default layout on the main workload, per mode;
   hosvd    the HOSVD start on the main workload.
 --impl reference times the FP64 CPU oracle (the stand-in for the paper's CPU
 implementation) on the host cores on a bounded sample of the same workload.
@@ -67,7 +69,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-hosvd", action="store_true", help="skip the HOSVD-initialisation timing")
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision legs (forms, c3, c4)")
-    ap.add_argument("--legs", default="forms,c3,c4,sweeps,serve,hosvd",
+    ap.add_argument("--legs", default="forms,autotune,c3,c4,sweeps,serve,hosvd",
                     help="comma list of the legs to run after the main measurement")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving mix to stream through the server (0: skip)")
@@ -475,6 +477,44 @@ def forms_leg(hoqri, torch, X, U0, cfg, stream, steps, warmup, peaks, nsm, cfg_n
     return res
 
 
+def autotune_leg(hoqri, torch, X, U0, cfg, stream, steps, warmup, reps=5):
+    """The autotuner on the main workload: a default and an autotuned FP32
+    context (the tuner times lane tiles and layouts of every mode at create);
+    per mode the time of hoqri_ttmctc (its core refresh and TTMcTC pass, CUDA
+    events, mean of `reps`), the chosen layout, the sweep time and the create
+    time (tuning included)."""
+    N = X.N
+    ranks = cfg["ranks"]
+    res = {"workload": config_block_str("c2" if N == 3 else "main", cfg, X.nnz),
+           "layout_fields": "long-row threshold, work-item size, tile rows, tile cols"}
+    for name, at in (("default", 0), ("autotuned", 1)):
+        t0 = time.perf_counter()
+        c = _ctx(hoqri, torch, X, U0, ranks, 1, stream, autotune=at)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        try:
+            per_mode = []
+            for n in range(N):
+                A = torch.empty((X.dims[n], ranks[n]), dtype=torch.float32, device="cuda")
+                hoqri.hoqri_ttmctc(c, n, A)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    hoqri.hoqri_ttmctc(c, n, A)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                per_mode.append(e0.elapsed_time(e1) / reps)
+                del A
+            ms = timed_sweeps(hoqri, torch, c, stream, steps, warmup)
+            res[name] = {"ttmctc_ms_per_mode": per_mode, "layouts": [list(hoqri.hoqri_layout(c, n)) for n in range(N)],
+                         "ms_per_sweep": ms / steps, "create_s": t_create}
+        finally:
+            hoqri.hoqri_destroy(c)
+    res["sweep_speedup"] = res["default"]["ms_per_sweep"] / res["autotuned"]["ms_per_sweep"]
+    return res
+
+
 def _subspace(Ut, U):
     """Largest principal angle (degrees) between span(Ut) and span(U), and the
     distance min_Q ||U - Ut Q||_F of Sec. 5 (orthonormal U, Ut)."""
@@ -752,6 +792,8 @@ def run_ours(args):
     if side and "forms" in legs and prec != hoqri.HOQRI_FP64:
         leg("forms", lambda: forms_leg(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup, peaks, nsm,
                                        args.config, orc))
+    if side and "autotune" in legs and prec == hoqri.HOQRI_FP32:
+        leg("autotune", lambda: autotune_leg(hoqri, torch, X, U0, cfg, stream, args.steps, args.warmup))
     if side and "hosvd" in legs:
         leg("init_hosvd", lambda: hosvd_init(hoqri, torch, X, U0, cfg, stream, prec))
     if side and "c3" in legs:

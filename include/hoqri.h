@@ -90,10 +90,15 @@ typedef struct {
     uint64_t seed;      /* seed of the initial factors when U0 is NULL */
     double tol;         /* hoqri_run: stop after the first sweep whose residual differs
                            from the previous one by less than tol (0: never) */
+    int32_t tile_rows;  /* FP32 sliced pass: accumulators per lane along the Kronecker
+                           prefix (8 or 4) and along the last mode (tile_cols, 8 or 4),
+                           for every mode whose plan allows it; 0, 0: the plan's tile
+                           (8 x 8 where the ranks allow), or the autotuner's choice */
+    int32_t tile_cols;
 } hoqri_options;
 
 /* Fills *opt with the defaults (FP32, CholeskyQR2 + fallback, library-chosen
- * chunk, no autotune, graphs on, seed 0, tol 0). */
+ * chunk, no autotune, graphs on, seed 0, tol 0, the plan's lane tile). */
 HOQRI_API void hoqri_default_options(hoqri_options *opt);
 
 /*
@@ -199,6 +204,14 @@ HOQRI_API hoqri_status hoqri_fit(hoqri_ctx *ctx, double *resid, double *normX2, 
 /* Sizes after set-up (host pointers, each may be NULL): nnz after summing
  * repeats; rows[N] = number of non-empty mode-n slices; device bytes held. */
 HOQRI_API hoqri_status hoqri_info(hoqri_ctx *ctx, int64_t *nnz, int64_t *rows, int64_t *device_bytes);
+
+/* The nonzero-stream layout mode `mode` runs with (host, NULL allowed, 4 values):
+ * the row length above which a row is streamed contiguously, the work-item size
+ * (nonzeros), and the rows and columns of the FP32 lane tile; all -1 when the
+ * mode does not use the sliced pass (two-pass kernels or the fiber pass).  Not
+ * in the paper (a property of this implementation's gather layout; the
+ * autotuner's choices are read here). */
+HOQRI_API hoqri_status hoqri_layout(hoqri_ctx *ctx, int32_t mode, int64_t *out4);
 
 /* Tracing: enable = 1 clears the totals and starts recording a CUDA event pair
  * around every core pass, TTMcTC pass, QR and nonzero-stream kernel on the

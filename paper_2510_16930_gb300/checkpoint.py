@@ -2,7 +2,7 @@
 
 A checkpoint holds the factors U_1..U_N, the number of sweeps run, the
 residual history, every field of the context's options (precision, QR kind,
-task size, autotune, graphs, one-stream form, seed, tolerance), and the
+task size, autotune, graphs, one-stream form, seed, tolerance, lane tile), and the
 tensor's dims and ranks (``numpy.savez``; the tensor itself is not stored: the
 caller supplies the same nonzeros on resume).  Resuming creates a context from
 the tensor with the saved factors as its initial factors and the saved
@@ -27,7 +27,8 @@ import numpy as np
 from . import hoqri
 
 FORMAT = 2
-OPTION_FIELDS = ("prec", "qr_kind", "chunk_nnz", "autotune", "use_graphs", "one_stream", "seed", "tol")
+OPTION_FIELDS = ("prec", "qr_kind", "chunk_nnz", "autotune", "use_graphs", "one_stream", "seed", "tol", "tile_rows",
+                 "tile_cols")
 
 
 def save(path, factors, *, dims, ranks, prec, sweeps, resid_hist=None, seed=0, options=None):

@@ -424,6 +424,17 @@ hoqri_status hoqri_create(hoqri_ctx **out, int32_t N, const int64_t *dims, const
     if ((s = dalloc(c, &c->G, c->P * c->rsize)) != HOQRI_OK) return fail(s);
     if ((s = dalloc(c, &c->A, maxIK * c->rsize)) != HOQRI_OK) return fail(s);
     if ((s = qr_init(c)) != HOQRI_OK) return fail(s);
+    if (c->opt.tile_rows > 0 || c->opt.tile_cols > 0) {
+        const int tl = c->opt.tile_rows, tv = c->opt.tile_cols;
+        if ((tl != 4 && tl != 8) || (tv != 4 && tv != 8)) {
+            set_error("hoqri_create: tile_rows and tile_cols must be 4 or 8 (or both 0)");
+            return fail(HOQRI_ERR_INVALID);
+        }
+        for (int n = 0; n < N; ++n) {
+            c->ms[n].tune_TL = tl;
+            c->ms[n].tune_TV = tv;
+        }
+    }
     if ((s = passes_init(c)) != HOQRI_OK) return fail(s);
     {
         // the two-pass core is computed from the mode of least nnz P_{-m} + R_m P
@@ -790,6 +801,23 @@ hoqri_status hoqri_info(hoqri_ctx *c, int64_t *nnz, int64_t *rows, int64_t *devi
     if (rows)
         for (int n = 0; n < c->N; ++n) rows[n] = c->ms[n].R;
     if (device_bytes) *device_bytes = c->device_bytes;
+    return HOQRI_OK;
+}
+
+hoqri_status hoqri_layout(hoqri_ctx *c, int32_t mode, int64_t *out4) {
+    g_last_error.clear();
+    HQ_TRY(check_mode(c, mode));
+    if (!out4) return HOQRI_OK;
+    const ModeStore &M = c->ms[mode];
+    FastTile p;
+    if (!M.hyb || !hyb_mode(c, mode) || !hyb_tile(c, mode, &p)) {
+        for (int q = 0; q < 4; ++q) out4[q] = -1;
+        return HOQRI_OK;
+    }
+    out4[0] = M.tune_Lshort;
+    out4[1] = M.tune_T;
+    out4[2] = p.TL;
+    out4[3] = p.TV;
     return HOQRI_OK;
 }
 

@@ -1022,7 +1022,26 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
 
 }  // namespace
 
-bool hyb_tile(const hoqri_ctx *c, int n, FastTile *out) { return fast_tile(c, n, out); }
+// the register-tile plan of mode n, with the lane tile the autotuner chose if any
+// (FP32 only: the split-BF16 tiles keep the plan's 8 x 8)
+bool hyb_tile(const hoqri_ctx *c, int n, FastTile *out) {
+    FastTile p;
+    if (!fast_tile(c, n, &p)) return false;
+    const ModeStore &M = c->ms[n];
+    if (!c->mix && M.tune_TL > 0 && M.tune_TV > 0) {
+        const int L = p.GL * p.TL;
+        if (L % M.tune_TL == 0 && p.Kl % M.tune_TV == 0 && (L / M.tune_TL) * (p.Kl / M.tune_TV) <= 32 &&
+            (p.nm1 == 2 || p.Kb % M.tune_TL == 0)) {  // order 4: a lane's rows stay in one K_b block
+            p.TL = M.tune_TL;
+            p.TV = M.tune_TV;
+            p.GL = L / p.TL;
+            p.GV = p.Kl / p.TV;
+            p.lpn = p.GL * p.GV;
+        }
+    }
+    *out = p;
+    return true;
+}
 
 int hyb_blocks_per_sm(const FastTile &p) {
     (void)p;

@@ -95,6 +95,7 @@ struct ModeStore {
     int64_t nspan = 0;
     int32_t *span = nullptr;             // [3*nspan] (long row j, first range, last range) of rows cut by ranges
     int64_t tune_Lshort = 0, tune_T = 0; // the layout parameters it was built with
+    int tune_TL = 0, tune_TV = 0;        // lane tile of the FP32 pass (0: the plan's own)
     int64_t long_elems = 0;              // nonzeros in the long part
     int64_t hyb_bytes = 0;               // device bytes of the hybrid arrays
 

@@ -24,7 +24,7 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 # every entry point declared in include/hoqri.h
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
            "hoqri_iterate", "hoqri_run", "hoqri_grad_norm2", "hoqri_init_hosvd",
-           "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info",
+           "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_layout",
            "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
            "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
            "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take", "hoqri_server_destroy")
@@ -33,7 +33,8 @@ HOQRI_REQ_QUEUED, HOQRI_REQ_RUNNING, HOQRI_REQ_DONE, HOQRI_REQ_FAILED = range(4)
 
 class hoqri_options(C.Structure):
     _fields_ = [("prec", C.c_int32), ("qr_kind", C.c_int32), ("chunk_nnz", C.c_int32), ("autotune", C.c_int32),
-                ("use_graphs", C.c_int32), ("one_stream", C.c_int32), ("seed", C.c_uint64), ("tol", C.c_double)]
+                ("use_graphs", C.c_int32), ("one_stream", C.c_int32), ("seed", C.c_uint64), ("tol", C.c_double),
+                ("tile_rows", C.c_int32), ("tile_cols", C.c_int32)]
 
 
 class hoqri_request(C.Structure):
@@ -81,6 +82,7 @@ def load(build_if_missing: bool = True):
     L.hoqri_set_factor.argtypes = [vp, i32, vp]
     L.hoqri_fit.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.hoqri_info.argtypes = [vp, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]
+    L.hoqri_layout.argtypes = [vp, i32, C.POINTER(i64)]
     L.hoqri_profile_enable.argtypes = [vp, i32]
     L.hoqri_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
     L.hoqri_synchronize.argtypes = [vp]
@@ -97,7 +99,7 @@ def load(build_if_missing: bool = True):
     L.hoqri_destroy.restype = None
     for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate", "hoqri_run",
                  "hoqri_grad_norm2", "hoqri_init_hosvd",
-                 "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_synchronize",
+                 "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_layout", "hoqri_synchronize",
                  "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
                  "hoqri_server_submit", "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take"):
         getattr(L, name).restype = C.c_int
@@ -214,6 +216,14 @@ def hoqri_info(ctx, N):
     rows = (C.c_int64 * N)()
     _check(load().hoqri_info(ctx, C.byref(nnz), rows, C.byref(b)))
     return nnz.value, list(rows), b.value
+
+
+def hoqri_layout(ctx, mode):
+    """(long-row threshold, work-item size, tile rows, tile columns) of the mode's
+    sliced pass, or all -1 when the mode does not use it."""
+    out = (C.c_int64 * 4)()
+    _check(load().hoqri_layout(ctx, int(mode), out))
+    return tuple(out)
 
 
 def hoqri_profile_enable(ctx, enable=True):

@@ -28,7 +28,7 @@ def test_library_exports_all_symbols():
 def test_default_options_and_error_text():
     o = hoqri.hoqri_default_options()
     assert o.prec == hoqri.HOQRI_FP32 and o.qr_kind == 0 and o.use_graphs == 1
-    assert ctypes.sizeof(hoqri.hoqri_options) == 40
+    assert ctypes.sizeof(hoqri.hoqri_options) == 48 and o.tile_rows == 0 and o.tile_cols == 0
     assert isinstance(hoqri.hoqri_last_error(), str)
 
 
