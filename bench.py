@@ -455,6 +455,18 @@ def forms_leg(hoqri, torch, X, U0, cfg, stream, steps, warmup, peaks, nsm, cfg_n
         res[name]["fit_rel_err_vs_fp64_max"] = float(e.max())
         res[name]["fit_rel_err_vs_fp64_final"] = float(e[-1])
     res["speedup_bf16x3_over_fp32"] = res["bf16x3"]["value"] / res["fp32"]["value"]
+    # the paper's O(IK)-memory form (Table 2): a separate core pass over the
+    # nonzeros and no stored Y_(n), beside the stored-Y form of the FP32 path
+    for name, os_ in (("fp32_stored_y", 0), ("fp32_o_ik", 2)):
+        c = _ctx(hoqri, torch, X, U0, ranks, 1, stream, one_stream=os_)
+        try:
+            nnz_c, _, dev_b = hoqri.hoqri_info(c, N)
+            ms = timed_sweeps(hoqri, torch, c, stream, max(3, steps // 4), warmup)
+            res.setdefault("memory_forms", {})[name] = {
+                "value": nnz_c * N * max(3, steps // 4) / (ms / 1e3), "unit": UNIT,
+                "ms_per_step": ms / max(3, steps // 4), "device_bytes": dev_b}
+        finally:
+            hoqri.hoqri_destroy(c)
     if orc is not None:
         vo = np.ascontiguousarray(X.vals, dtype=np.float64)
         U64 = [np.asarray(u, dtype=np.float64) for u in U0]

@@ -122,6 +122,7 @@ static void destroy_impl(hoqri_ctx *c) {
         dfree(M.fb_rrow0, st);
         dfree(M.fb_span, st);
         dfree(c->U[n], st);
+        dfree(c->Upad[n], st);
     }
     dfree(c->gslot, st);
     dfree(c->gcount, st);

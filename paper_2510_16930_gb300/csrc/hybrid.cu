@@ -908,6 +908,17 @@ __global__ void __launch_bounds__(256) k_core_from_y2(const float *Y, const floa
     }
 }
 
+// Upad(i, k) = U(i, k) for k < K, 0 for K <= k < Kp: the factor as the sliced
+// pass of a padded plan gathers it
+__global__ void k_pad_factor(const float *U, int64_t rows, int K, int Kp, float *Upad) {
+    const int64_t n = rows * Kp;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = t / Kp;
+        const int k = (int)(t - r * Kp);
+        Upad[t] = k < K ? U[r * K + k] : 0.f;
+    }
+}
+
 struct HybLaunch {
     size_t smem = 0;
     int hw = 0;
@@ -925,10 +936,9 @@ void mix_shape(const hoqri_ctx *c, int n, const FastTile &p, int *MT, int *NT) {
     *MT = 0;
     *NT = 0;
     if (!c->mix || p.TL != 8 || p.TV != 8) return;
-    int K3[3] = {0, 0, 0}, j = 0;
-    for (int m = 0; m < c->N; ++m)
-        if (m != n) K3[j++] = c->K[m];
-    const int Kl = K3[p.nm1 - 1];
+    (void)n;
+    const int K3[3] = {p.Ka, p.nm1 == 3 ? p.Kb : p.Kl, p.Kl};  // the plan's (possibly padded) ranks
+    const int Kl = p.Kl;
     if (Kl != 8 && Kl != 16 && Kl != 32) return;
     if (p.nm1 == 2 && (K3[0] == 16 || K3[0] == 32)) {
         *MT = K3[0] / 16;
@@ -1024,9 +1034,13 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
 
 // the register-tile plan of mode n, with the lane tile the autotuner chose if any
 // (FP32 only: the split-BF16 tiles keep the plan's 8 x 8)
+bool padded_plan(const hoqri_ctx *c, int n, FastTile *out);  // passes.cu
+
 bool hyb_tile(const hoqri_ctx *c, int n, FastTile *out) {
     FastTile p;
-    if (!fast_tile(c, n, &p)) return false;
+    // ranks that are not powers of two >= 4: the plan of the padded ranks (the
+    // pass gathers zero-padded factor copies; the padded columns of Y_(n) are 0)
+    if (!fast_tile(c, n, &p) && !padded_plan(c, n, &p)) return false;
     const ModeStore &M = c->ms[n];
     if (!c->mix && M.tune_TL > 0 && M.tune_TV > 0) {
         const int L = p.GL * p.TL;
@@ -1099,7 +1113,18 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
         for (int m = 0; m < c->N; ++m)
             if (m != n) {
                 Uo[j] = (const float *)c->U[m];
-                Ko[j++] = c->K[m];
+                Ko[j] = c->K[m];
+                if (p.pad && padded_rank(c->K[m]) != c->K[m]) {
+                    // refresh the zero-padded copy from the current factor
+                    const int Kp = padded_rank(c->K[m]);
+                    const int64_t tot = c->dims[m] * (int64_t)Kp;
+                    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(tot, 256), 8 * (int64_t)c->num_sms));
+                    k_pad_factor<<<g, 256, 0, c->stream>>>((const float *)c->U[m], c->dims[m], c->K[m], Kp, c->Upad[m]);
+                    c->nlaunch++;
+                    Uo[j] = c->Upad[m];
+                    Ko[j] = Kp;
+                }
+                ++j;
             }
         a.Ua = Uo[0];
         a.Ub = Uo[1];
@@ -1116,7 +1141,7 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
                 if (m != n) ml = m;
             const int64_t rows = c->dims[ml];
             const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(rows * Kl / 2, 256), 8 * (int64_t)c->num_sms));
-            k_split_bf16<<<grid, 256, 0, c->stream>>>((const float *)c->U[ml], rows, Kl, (uint32_t *)c->usplit);
+            k_split_bf16<<<grid, 256, 0, c->stream>>>(Uo[p.nm1 - 1], rows, Kl, (uint32_t *)c->usplit);
             c->nlaunch++;
             a.Ulsplit = (const float *)c->usplit;
         }
@@ -1140,11 +1165,13 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     return HOQRI_OK;
 }
 
-// A_n = Y_(n) G_(n)^T from the stored rows (Gn: G_(n) as [Kn][Pm] on the device).
+// A_n = Y_(n) G_(n)^T from the stored rows (Gn: G_(n) as [Kn][Pm] on the device,
+// over the padded columns when the mode's plan is padded).
 hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
     const ModeStore &M = c->ms[n];
     const int Kn = c->K[n];
-    const int Pm = (int)(c->P / Kn);
+    FastTile pl;
+    const int Pm = hyb_tile(c, n, &pl) ? pl.Pm : (int)(c->P / Kn);
     const int Knp = (Kn + 3) & ~3;
     const int RT = std::min(256, 4 * (256 / (Knp / 4)));
     const int EC = Pm < 32 ? Pm : 32;
@@ -1184,7 +1211,8 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
 hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
     const ModeStore &M = c->ms[n];
     const int Kn = c->K[n];
-    const int Pm = (int)(c->P / Kn);
+    FastTile pl;
+    const int Pm = hyb_tile(c, n, &pl) ? pl.Pm : (int)(c->P / Kn);
     const int Knp = (Kn + 3) & ~3;
     const int64_t R = M.R;
     int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),

@@ -138,6 +138,8 @@ struct hoqri_ctx {
     int64_t nnz = 0;                    // after summing repeats
     hoqri::ModeStore ms[HOQRI_MAXN];
     void *U[HOQRI_MAXN] = {};           // factors, real[I_n*K_n]
+    float *Upad[HOQRI_MAXN] = {};       // zero-padded copies I_n x padded_rank(K_n) for the sliced
+                                        // pass of modes whose other ranks are not powers of two >= 4
     void *G = nullptr;                  // real[P]
     void *A = nullptr;                  // real[max I_n*K_n], TTMcTC output of the sweep
     // FP64 scalars on the device: [0] ||X||^2, [1] ||G||^2 of the last core,
@@ -213,7 +215,12 @@ struct FastTile {
     bool ok = false;
     int nm1 = 0, TL = 0, TV = 0, GL = 0, GV = 0, lpn = 0;
     int Ka = 0, Kb = 0, Kl = 0, Pm = 0;
+    // sliced pass only: ranks of the other modes rounded up to powers of two >= 4
+    // (the factors are gathered from zero-padded copies; Ka, Kb, Kl, Pm are padded)
+    bool pad = false;
 };
+// rank of mode m's factor as the sliced pass gathers it (a power of two >= 4)
+int padded_rank(int K);
 bool fast_tile(const hoqri_ctx *c, int n, FastTile *out);
 // tile of the hybrid (sliced) pass for mode n: the plan above with at most 32
 // FP32 accumulators per lane where the shape allows (three blocks per SM)

@@ -527,20 +527,26 @@ __global__ void __launch_bounds__(128) k_fixup(const int32_t *big, const int32_t
     }
 }
 
+// Entries of the unfolding G_(n) as [Kn][Pm] (the partial and unfolded layouts)
+// against the row-major core.  The sliced pass of a padded plan works on columns
+// over the padded ranks KoP (PmP columns); columns with a padded index are not
+// entries of G (their sums are zero).
 struct CoreMap {
-    int nm1, Kn, Pm;
-    int Ko[HOQRI_MAXN - 1];
+    int nm1, Kn, Pm, PmP;
+    int Ko[HOQRI_MAXN - 1], KoP[HOQRI_MAXN - 1];
     int64_t gso[HOQRI_MAXN - 1];
     int64_t gsn;
 };
 
+// row-major index of unfolded entry p (over the padded columns), -1 for a padded column
 __device__ __forceinline__ int64_t rowmajor_of(const CoreMap &m, int p) {
-    int kn = p / m.Pm;
-    int e = p - kn * m.Pm;
+    int kn = p / m.PmP;
+    int e = p - kn * m.PmP;
     int64_t g = (int64_t)kn * m.gsn;
     for (int j = m.nm1 - 1; j >= 0; --j) {
-        int k = e % m.Ko[j];
-        e /= m.Ko[j];
+        int k = e % m.KoP[j];
+        e /= m.KoP[j];
+        if (k >= m.Ko[j]) return -1;
         g += (int64_t)k * m.gso[j];
     }
     return g;
@@ -554,7 +560,7 @@ __device__ __forceinline__ int64_t rowmajor_of(const CoreMap &m, int p) {
 template <typename T>
 __global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nblk, CoreMap m, T *G, double *gpart) {
     __shared__ double sh[RED_TPB / 32][33];
-    const int P = m.Kn * m.Pm;
+    const int P = m.Kn * m.PmP;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = RED_TPB / 32;
     const int p = blockIdx.x * 32 + lane;
     double s = 0.0;
@@ -566,8 +572,9 @@ __global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nbl
         double t = 0.0;
         for (int q = 0; q < nw; ++q) t += sh[q][lane];
         double sq = 0.0;
-        if (p < P) {
-            G[rowmajor_of(m, p)] = (T)t;
+        const int64_t g = p < P ? rowmajor_of(m, p) : -1;
+        if (g >= 0) {
+            G[g] = (T)t;
             sq = t * t;  // the FP64 sum, before the entry is rounded to T
         }
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -591,8 +598,11 @@ __global__ void k_sum_into(const double *part, int n, double *out, double *out2)
 // Gn[kn][e] = G(row-major) for the TTMcTC pass
 template <typename T>
 __global__ void k_core_to_unfolded(const T *G, CoreMap m, T *Gn) {
-    const int P = m.Kn * m.Pm;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) Gn[p] = G[rowmajor_of(m, p)];
+    const int P = m.Kn * m.PmP;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        const int64_t g = rowmajor_of(m, p);
+        Gn[p] = g >= 0 ? G[g] : T(0);
+    }
 }
 
 // ------------------------------------------------------------ host side
@@ -610,9 +620,25 @@ CoreMap core_map(hoqri_ctx *c, int n) {
     for (int q = 0; q < c->N; ++q) {
         if (q == n) continue;
         m.Ko[j] = c->K[q];
+        m.KoP[j] = c->K[q];
         m.gso[j] = st[q];
         m.Pm *= c->K[q];
         ++j;
+    }
+    m.PmP = m.Pm;
+    return m;
+}
+
+// the map of the sliced pass of mode n: over padded columns when its plan is padded
+CoreMap core_map_hyb(hoqri_ctx *c, int n) {
+    CoreMap m = core_map(c, n);
+    FastTile p;
+    if (hyb_tile(c, n, &p) && p.pad) {
+        m.PmP = 1;
+        for (int j = 0; j < m.nm1; ++j) {
+            m.KoP[j] = padded_rank(m.Ko[j]);
+            m.PmP *= m.KoP[j];
+        }
     }
     return m;
 }
@@ -644,15 +670,12 @@ int gen_block_core(int Pm, int Kl, int Kn, int rtot, size_t rsize) {
 
 bool pow2_ge4(int k) { return k >= 4 && k <= 64 && (k & (k - 1)) == 0; }
 
-FastTile fast_plan(const hoqri_ctx *c, int n) {
+// register-tile plan from the ranks of the other modes (powers of two >= 4)
+FastTile plan_of(int N, const int (&Ko)[3]) {
     FastTile p;
-    if (c->prec != HOQRI_FP32 || (c->N != 3 && c->N != 4)) return p;
-    int Ko[3], j = 0;
-    for (int m = 0; m < c->N; ++m)
-        if (m != n) Ko[j++] = c->K[m];
-    for (int q = 0; q < j; ++q)
+    for (int q = 0; q < N - 1; ++q)
         if (!pow2_ge4(Ko[q])) return p;
-    p.nm1 = c->N - 1;
+    p.nm1 = N - 1;
     p.Kl = Ko[p.nm1 - 1];
     p.TV = std::min(8, p.Kl);
     p.GV = p.Kl / p.TV;
@@ -673,6 +696,15 @@ FastTile fast_plan(const hoqri_ctx *c, int n) {
     if (p.lpn > 32) return p;
     p.ok = true;
     return p;
+}
+
+FastTile fast_plan(const hoqri_ctx *c, int n) {
+    FastTile p;
+    if (c->prec != HOQRI_FP32 || (c->N != 3 && c->N != 4)) return p;
+    int Ko[3] = {0, 0, 0}, j = 0;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) Ko[j++] = c->K[m];
+    return plan_of(c->N, Ko);
 }
 
 template <typename T>
@@ -921,6 +953,32 @@ hoqri_status ttmctc_pass_t(hoqri_ctx *c, int n, const void *G, void *A_out) {
 
 int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+int padded_rank(int K) {
+    int k = 4;
+    while (k < K) k <<= 1;
+    return k;
+}
+
+// the plan of the sliced pass over padded ranks (FP32 storage, orders 3 and 4);
+// ok only when some other rank actually needs padding
+bool padded_plan(const hoqri_ctx *c, int n, FastTile *out) {
+    if (c->prec != HOQRI_FP32 || (c->N != 3 && c->N != 4)) return false;
+    int Ko[3] = {0, 0, 0}, j = 0;
+    bool any = false;
+    for (int m = 0; m < c->N; ++m)
+        if (m != n) {
+            Ko[j] = padded_rank(c->K[m]);
+            any = any || Ko[j] != c->K[m];
+            ++j;
+        }
+    if (!any) return false;
+    FastTile p = plan_of(c->N, Ko);
+    if (!p.ok) return false;
+    p.pad = true;
+    *out = p;
+    return true;
+}
+
 bool fast_tile(const hoqri_ctx *c, int n, FastTile *out) {
     FastTile p = fast_plan(c, n);
     if (!p.ok) return false;
@@ -929,8 +987,8 @@ bool fast_tile(const hoqri_ctx *c, int n, FastTile *out) {
 }
 
 hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *normG2_slot) {
-    CoreMap m = core_map(c, n);
-    const int KnPm = m.Kn * m.Pm;
+    CoreMap m = core_map_hyb(c, n);
+    const int KnPm = m.Kn * m.PmP;
     const int rb = (KnPm + 31) / 32;
     if (c->prec == HOQRI_FP64)
         k_core_reduce<double><<<rb, RED_TPB, 0, c->stream>>>((const double *)c->core_part, nblk, m, (double *)G_out,
@@ -945,8 +1003,8 @@ hoqri_status core_reduce(hoqri_ctx *c, int n, int nblk, void *G_out, double *nor
 }
 
 hoqri_status unfold_core(hoqri_ctx *c, int n, const void *G, void *Gn) {
-    CoreMap m = core_map(c, n);
-    const int KnPm = m.Kn * m.Pm;
+    CoreMap m = core_map_hyb(c, n);
+    const int KnPm = m.Kn * m.PmP;
     const int g = std::max(1, std::min(64, (KnPm + 255) / 256));
     if (c->prec == HOQRI_FP64)
         k_core_to_unfolded<double><<<g, 256, 0, c->stream>>>((const double *)G, m, (double *)Gn);
@@ -1007,7 +1065,7 @@ hoqri_status passes_init(hoqri_ctx *c) {
     // ~16 work items per resident warp (8 warps per SM) for balance across SMs
     const int64_t Tt = std::max<int64_t>(256, std::min<int64_t>(16384, ceil_div(c->nnz, (int64_t)c->num_sms * 128)));
     const int64_t T32 = (Tt + 31) & ~(int64_t)31;
-    int64_t fpb = 0;
+    int64_t fpb = 0, core_pad = 0, gn_pad = 0;
     for (int n = 0; n < c->N; ++n) {
         if (c->opt.one_stream == 2) continue;
         if (c->opt.one_stream == 3 && fib_shape(c, n, nullptr)) {
@@ -1024,6 +1082,13 @@ hoqri_status passes_init(hoqri_ctx *c) {
         const ModeStore &M = c->ms[n];
         ab = std::max<int64_t>(ab, std::max<int64_t>(M.nitem_long, 1) * 2 * c->K[n] * (int64_t)c->rsize);
         ybytes = std::max<int64_t>(ybytes, M.R * (int64_t)p.Pm * 4);
+        // partials of G_(n) over padded columns (k_core_from_y*: at most 2 CTAs per SM)
+        core_pad = std::max<int64_t>(core_pad, (int64_t)2 * c->num_sms * c->K[n] * p.Pm * 4);
+        gn_pad = std::max<int64_t>(gn_pad, (int64_t)c->K[n] * p.Pm);
+        if (p.pad)
+            for (int m = 0; m < c->N; ++m)
+                if (m != n && padded_rank(c->K[m]) != c->K[m] && !c->Upad[m])
+                    HQ_TRY(dalloc(c, (void **)&c->Upad[m], (size_t)c->dims[m] * padded_rank(c->K[m]) * sizeof(float)));
         // pieces of rows cut by warp ranges: at most one range per warp of the pass
         // (any layout the autotuner may build)
         ypb = std::max<int64_t>(ypb, (int64_t)c->num_sms * HY_BLOCKS_PER_SM * 8 * 2 * (int64_t)p.Pm * 4);
@@ -1045,11 +1110,18 @@ hoqri_status passes_init(hoqri_ctx *c) {
         for (int n = 0; n < c->N; ++n)
             if (c->ms[n].fib) free_fiber(c, n);
     }
-    HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((c->P + 31) / 32 + 1) * sizeof(double)));
+    if (core_pad > c->core_part_bytes) {
+        // the sliced pass of a padded plan writes wider partials than the two-pass core
+        dfree(c->core_part, c->stream);
+        c->device_bytes -= c->core_part_bytes;
+        c->core_part_bytes = core_pad;
+        HQ_TRY(dalloc(c, &c->core_part, c->core_part_bytes));
+    }
+    HQ_TRY(dalloc(c, (void **)&c->gnorm_part, ((std::max<int64_t>(c->P, gn_pad) + 31) / 32 + 1) * sizeof(double)));
     HQ_TRY(dalloc(c, (void **)&c->claim, sizeof(unsigned long long)));
     if (c->mix && c->Y) {
         int64_t sb = 0;
-        for (int m = 0; m < c->N; ++m) sb = std::max<int64_t>(sb, c->dims[m] * c->K[m] * 4);
+        for (int m = 0; m < c->N; ++m) sb = std::max<int64_t>(sb, c->dims[m] * padded_rank(c->K[m]) * 4);
         HQ_TRY(dalloc(c, &c->usplit, sb));
     }
     return HOQRI_OK;

@@ -102,7 +102,7 @@ hoqri_status autotune_hybrid(hoqri_ctx *c) {
         ModeStore &M = c->ms[n];
         if (!hyb_mode(c, n) || !M.hyb) continue;
         FastTile p0;
-        if (!fast_tile(c, n, &p0)) continue;
+        if (!hyb_tile(c, n, &p0)) continue;
         const int64_t T0 = M.tune_T, L0 = M.tune_Lshort;
         const double long_share = c->nnz > 0 ? (double)M.long_elems / (double)c->nnz : 0.0;
         const std::string key = tune_key(c, n, long_share);
