@@ -565,346 +565,69 @@ __global__ void __launch_bounds__(HY_WARPS * 32, 2) k_hyb(HybArgs a) {
     }
 }
 
-// Y rows of the long rows cut by warp-range boundaries.  Piece of range t0
-// (slot s0) and pieces of ranges t0+1..t1 (slot 0) are summed: warp w adds the
-// pieces t0+1+w, t0+1+w+8, ... in order, then the 8 warp sums and the first
-// piece are added in a fixed order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) k_span_fix(const int32_t *span, const int32_t *lrow, const int32_t *item_aux,
-                                                  int64_t ipw, const float *ypart, int Pm, float *Y) {
-    extern __shared__ __align__(16) float part[];  // [8][Pm]
+// Y rows of the long rows cut by warp-range boundaries.  The row's piece from
+// range t0 (slot s0) and its pieces from ranges t0+1..t1 (slot 0) are summed.
+// Thread (j, c) adds the 16-byte column group c of pieces t0+1+j, t0+1+j+ns,
+// ... (ns = SF_THREADS / (Pm/4) piece streams, at most 32, at least 1) in
+// SF_ACC interleaved running sums, so that SF_ACC loads are in flight (a
+// Zipf-heavy row spans hundreds of ranges), combined in a fixed order; then
+// the ns stream sums and the first piece are added in order, in FP64.  The
+// result does not depend on scheduling.
+constexpr int SF_THREADS = 256;
+constexpr int SF_ACC = 8;
+
+__host__ __device__ constexpr int span_fix_ns(int Pm) {
+    return SF_THREADS / (Pm / 4) < 1 ? 1 : (SF_THREADS / (Pm / 4) < 32 ? SF_THREADS / (Pm / 4) : 32);
+}
+
+__global__ void __launch_bounds__(SF_THREADS, 1) k_span_fix(const int32_t *span, const int32_t *lrow,
+                                                         const int32_t *item_aux, int64_t ipw, const float *ypart,
+                                                         int Pm, float *Y) {
+    extern __shared__ __align__(16) float4 part4[];  // [ns][Pm / 4]
     const int b = blockIdx.x;
     const int32_t jl = span[3 * b], t0 = span[3 * b + 1], t1 = span[3 * b + 2];
     const int s0 = (item_aux[(int64_t)t0 * ipw] == jl) ? 0 : 1;
     const int32_t r = lrow[jl];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int e = lane; e < Pm; e += 32) {
-        float s = 0.f;
-        for (int t = t0 + 1 + w; t <= t1; t += 8) s += ypart[((int64_t)t * 2) * Pm + e];
-        part[w * Pm + e] = s;
+    const int P4 = Pm >> 2;
+    const int ns = span_fix_ns(Pm);
+    const int cw = P4 < SF_THREADS ? P4 : SF_THREADS;  // column groups covered by one stream of threads
+    const int j = threadIdx.x / cw, c0 = threadIdx.x - j * cw;
+    const float4 *yp4 = reinterpret_cast<const float4 *>(ypart);
+    auto add4 = [](float4 &a, const float4 v) {
+        a.x += v.x;
+        a.y += v.y;
+        a.z += v.z;
+        a.w += v.w;
+    };
+    if (j < ns) {
+        for (int c = c0; c < P4; c += cw) {
+            float4 a[SF_ACC];
+#pragma unroll
+            for (int u = 0; u < SF_ACC; ++u) a[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            int t = t0 + 1 + j;
+            for (; t + (SF_ACC - 1) * ns <= t1; t += SF_ACC * ns) {
+                float4 v[SF_ACC];
+#pragma unroll
+                for (int u = 0; u < SF_ACC; ++u) v[u] = yp4[(int64_t)(t + u * ns) * 2 * P4 + c];
+#pragma unroll
+                for (int u = 0; u < SF_ACC; ++u) add4(a[u], v[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < SF_ACC - 1; ++u)
+                if (t + u * ns <= t1) add4(a[u], yp4[(int64_t)(t + u * ns) * 2 * P4 + c]);
+#pragma unroll
+            for (int w = 1; w < SF_ACC; w *= 2)
+#pragma unroll
+                for (int u = 0; u < SF_ACC; u += 2 * w) add4(a[u], a[u + w]);
+            part4[j * P4 + c] = a[0];
+        }
     }
     __syncthreads();
+    const float *part = reinterpret_cast<const float *>(part4);
     for (int e = threadIdx.x; e < Pm; e += blockDim.x) {
         double s = ypart[((int64_t)t0 * 2 + s0) * Pm + e];
-        for (int q = 0; q < 8; ++q) s += part[q * Pm + e];
+        for (int q = 0; q < ns; ++q) s += part[q * Pm + e];
         Y[(int64_t)r * Pm + e] = (float)s;
-    }
-}
-
-// A(row_id[r], :) = G_(n) y_r for every stored row (the TTMcTC output, Eq.
-// ttmctc, from the rows of Y_(n)).  Register tiles of 4 rows x 4 values of k_n
-// per thread; Y and G_(n) are staged through shared memory in chunks of EC
-// columns.  Rows of A without nonzeros stay as cleared by the caller.
-__global__ void __launch_bounds__(256) k_a_from_y(const float *Y, const float *Gn, const int32_t *row_id, int64_t R,
-                                                  int Kn, int Knp, int Pm, int RT, float *A) {
-    extern __shared__ __align__(16) float dsm[];
-    const int EC = Pm < 32 ? Pm : 32;
-    float *YT = dsm;                    // [EC][RT + 4]
-    float *GT = dsm + EC * (RT + 4);    // [EC][Knp]
-    const int nkq = Knp >> 2;
-    const int t = threadIdx.x;
-    const int kq = t % nkq, rq = t / nkq;
-    const bool active = rq < (RT >> 2);
-    for (int64_t r0 = (int64_t)blockIdx.x * RT; r0 < R; r0 += (int64_t)gridDim.x * RT) {
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-        for (int e0 = 0; e0 < Pm; e0 += EC) {
-            __syncthreads();
-            const int nq = EC >> 2;
-            for (int idx = t; idx < RT * nq; idx += blockDim.x) {
-                const int rr = idx / nq, c4 = idx - rr * nq;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (r0 + rr < R) v = *reinterpret_cast<const float4 *>(Y + (r0 + rr) * Pm + e0 + 4 * c4);
-                YT[(4 * c4 + 0) * (RT + 4) + rr] = v.x;
-                YT[(4 * c4 + 1) * (RT + 4) + rr] = v.y;
-                YT[(4 * c4 + 2) * (RT + 4) + rr] = v.z;
-                YT[(4 * c4 + 3) * (RT + 4) + rr] = v.w;
-            }
-            for (int idx = t; idx < EC * Knp; idx += blockDim.x) {
-                const int e = idx / Knp, kn = idx - e * Knp;
-                GT[idx] = kn < Kn ? Gn[(size_t)kn * Pm + e0 + e] : 0.f;
-            }
-            __syncthreads();
-            if (active) {
-                for (int e = 0; e < EC; ++e) {
-                    const float4 y4 = *reinterpret_cast<const float4 *>(YT + e * (RT + 4) + 4 * rq);
-                    const float4 g4 = *reinterpret_cast<const float4 *>(GT + e * Knp + 4 * kq);
-                    const float yv[4] = {y4.x, y4.y, y4.z, y4.w};
-                    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-#pragma unroll
-                    for (int i = 0; i < 4; ++i)
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(yv[i], gv[k], acc[i][k]);
-                }
-            }
-        }
-        if (active) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int64_t r = r0 + 4 * rq + i;
-                if (r >= R) continue;
-                float *arow = A + (int64_t)row_id[r] * Kn;
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    if (4 * kq + k < Kn) arow[4 * kq + k] = acc[i][k];
-            }
-        }
-    }
-}
-
-// CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) * Y[r][e] over a
-// fixed row range per CTA (Sec. 2.2: G = U_n^T Y_(n)).  Each thread owns 4 x 4
-// (kn, e) tiles; U rows are staged in shared memory 64 at a time.
-__global__ void __launch_bounds__(256) k_core_from_y(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
-                                                     int Kn, int Knp, int Pm, int64_t rpb, float *cpart) {
-    constexpr int RB = 64;
-    extern __shared__ __align__(16) float Us[];  // [RB][Knp]
-    const int64_t r0 = (int64_t)blockIdx.x * rpb;
-    const int64_t r1 = min(r0 + rpb, R);
-    const int KnPm = Kn * Pm;
-    const int nkq = Knp >> 2, neq = Pm >> 2;
-    const int nasg = nkq * neq;
-    for (int base = 0; base < nasg; base += blockDim.x) {
-        const int asg = base + threadIdx.x;
-        const bool active = asg < nasg;
-        const int kq = active ? asg / neq : 0;
-        const int eq = active ? asg - kq * neq : 0;
-        float acc[4][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int k = 0; k < 4; ++k) acc[i][k] = 0.f;
-        for (int64_t rb = r0; rb < r1; rb += RB) {
-            const int nr = (int)min((int64_t)RB, r1 - rb);
-            __syncthreads();
-            for (int t = threadIdx.x; t < nr * Knp; t += blockDim.x) {
-                const int rr = t / Knp, q = t - rr * Knp;
-                Us[t] = q < Kn ? Un[(int64_t)row_id[rb + rr] * Kn + q] : 0.f;
-            }
-            __syncthreads();
-            if (active) {
-                // 8 rows at a time: their loads are all in flight before the FMAs
-                for (int rr0 = 0; rr0 < nr; rr0 += 8) {
-                    float4 yb[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        yb[u] = rr0 + u < nr ? __ldg(reinterpret_cast<const float4 *>(Y + (rb + rr0 + u) * Pm) + eq)
-                                             : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        if (rr0 + u >= nr) break;
-                        const float4 u4 = *reinterpret_cast<const float4 *>(Us + (rr0 + u) * Knp + 4 * kq);
-                        const float uv[4] = {u4.x, u4.y, u4.z, u4.w};
-                        const float yv[4] = {yb[u].x, yb[u].y, yb[u].z, yb[u].w};
-#pragma unroll
-                        for (int i = 0; i < 4; ++i)
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) acc[i][k] = fmaf(uv[i], yv[k], acc[i][k]);
-                    }
-                }
-            }
-        }
-        if (active) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int kn = 4 * kq + i;
-                if (kn >= Kn) continue;
-                float4 *dst = reinterpret_cast<float4 *>(cpart + (size_t)blockIdx.x * KnPm + (size_t)kn * Pm) + eq;
-                *dst = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-            }
-        }
-    }
-}
-
-// A(row_id[r], :) = G_(n) y_r for KN = K_n in {4, 8, 16, 32}: each CTA takes a
-// contiguous range of rows (equal ranges, one wave of CTAs), a thread two rows
-// (one for KN = 32) x all KN columns at a time.  G_(n) is staged transposed ([e][kn]) in shared
-// memory and read as broadcasts; the rows of Y stream in as 16-byte loads,
-// the next two vectors of each row issued before the current two are used,
-// so every thread keeps loads in flight while it multiplies (the kernel streams Y once and
-// is bound by HBM latency otherwise).
-constexpr int AY_EB = 2;
-
-template <int KN>
-__host__ __device__ constexpr int ay_rt() { return KN >= 32 ? 1 : 2; }  // rows per thread (KN = 32: registers)
-
-template <int KN, int AY_RT>
-__device__ __forceinline__ void ay_step(const float *Gt, int e, const float4 (&yv)[AY_RT],
-                                        float2 (&acc)[AY_RT][KN / 2]) {
-#pragma unroll
-    for (int ee = 0; ee < 4; ++ee) {
-        const float2 *g2 = reinterpret_cast<const float2 *>(Gt + (size_t)(e + ee) * KN);
-#pragma unroll
-        for (int k = 0; k < KN / 2; ++k) {
-            const float2 g = g2[k];
-#pragma unroll
-            for (int i = 0; i < AY_RT; ++i) {
-                const float yy = ee == 0 ? yv[i].x : (ee == 1 ? yv[i].y : (ee == 2 ? yv[i].z : yv[i].w));
-                acc[i][k] = __ffma2_rn(make_float2(yy, yy), g, acc[i][k]);
-            }
-        }
-    }
-}
-
-template <int KN>
-__global__ void __launch_bounds__(256, 2) k_a_from_y2(const float *Y, const float *Gn, const int32_t *row_id,
-                                                      int64_t R, int64_t rpb, int Pm, float *A) {
-    constexpr int AY_RT = ay_rt<KN>();
-    extern __shared__ __align__(16) float Gt[];  // [Pm][KN]
-    for (int t = threadIdx.x; t < Pm * KN; t += blockDim.x) {
-        const int e = t / KN, k = t - e * KN;
-        Gt[t] = Gn[(size_t)k * Pm + e];
-    }
-    __syncthreads();
-    const int64_t rbeg = (int64_t)blockIdx.x * rpb, rend = min(rbeg + rpb, R);
-    const int nb = Pm / (4 * AY_EB);  // full batches of AY_EB vectors per row
-    for (int64_t r0 = rbeg + (int64_t)threadIdx.x * AY_RT; r0 < rend; r0 += (int64_t)blockDim.x * AY_RT) {
-        float2 acc[AY_RT][KN / 2];
-#pragma unroll
-        for (int i = 0; i < AY_RT; ++i)
-#pragma unroll
-            for (int k = 0; k < KN / 2; ++k) acc[i][k] = make_float2(0.f, 0.f);
-        const float4 *yr[AY_RT];
-#pragma unroll
-        for (int i = 0; i < AY_RT; ++i) yr[i] = reinterpret_cast<const float4 *>(Y + (size_t)min(r0 + i, rend - 1) * Pm);
-        float4 cur[AY_EB][AY_RT], nxt[AY_EB][AY_RT];
-        if (nb > 0) {
-#pragma unroll
-            for (int b = 0; b < AY_EB; ++b)
-#pragma unroll
-                for (int i = 0; i < AY_RT; ++i) cur[b][i] = __ldg(yr[i] + b);
-        }
-        for (int bt = 0; bt < nb; ++bt) {
-            if (bt + 1 < nb) {
-#pragma unroll
-                for (int b = 0; b < AY_EB; ++b)
-#pragma unroll
-                    for (int i = 0; i < AY_RT; ++i) nxt[b][i] = __ldg(yr[i] + (bt + 1) * AY_EB + b);
-            }
-#pragma unroll
-            for (int b = 0; b < AY_EB; ++b) ay_step<KN, AY_RT>(Gt, 4 * (bt * AY_EB + b), cur[b], acc);
-#pragma unroll
-            for (int b = 0; b < AY_EB; ++b)
-#pragma unroll
-                for (int i = 0; i < AY_RT; ++i) cur[b][i] = nxt[b][i];
-        }
-        for (int e = nb * 4 * AY_EB; e < Pm; e += 4) {
-            float4 yv[AY_RT];
-#pragma unroll
-            for (int i = 0; i < AY_RT; ++i) yv[i] = __ldg(yr[i] + (e >> 2));
-            ay_step<KN, AY_RT>(Gt, e, yv, acc);
-        }
-#pragma unroll
-        for (int i = 0; i < AY_RT; ++i) {
-            if (r0 + i >= rend) break;
-            float2 *arow = reinterpret_cast<float2 *>(A + (size_t)row_id[r0 + i] * KN);
-#pragma unroll
-            for (int k = 0; k < KN / 2; ++k) arow[k] = acc[i][k];
-        }
-    }
-}
-
-// CTA partials of G_(n)[kn][e] = sum_r U_n(row_id[r], kn) Y[r][e] for KN in
-// {4, 8, 16, 32} and P_{-n} <= 1024: Pm/4 threads cover a row (4 columns of e
-// each, all KN rows of G), the block's ng row groups take every ng-th row of
-// the CTA's range, and the groups are added in group order at the end.  The
-// U rows of CY_CH rows at a time are gathered into one of two shared-memory
-// buffers while the previous CY_CH rows are multiplied; each group loads the Y
-// vectors of the next RB of its rows before it multiplies the current RB
-// (RB = 4; 2 for KN = 32, whose 32 accumulator vectors leave fewer registers).
-constexpr int CY_CH = 128;
-
-template <int KN, int RB = (KN >= 32 ? 2 : 4)>
-__global__ void __launch_bounds__(256) k_core_from_y2(const float *Y, const float *Un, const int32_t *row_id, int64_t R,
-                                                      int Pm, int64_t rpb, float *cpart) {
-    extern __shared__ __align__(16) float red[];  // [ng][KN * Pm] | Us [2][CY_CH][KN]
-    constexpr int UQ = KN / 4;                    // float4 per U row
-    constexpr int UPT = (CY_CH * UQ + 255) / 256;  // U vectors each thread stages per chunk
-    const int tpr = Pm >> 2;
-    const int ng = blockDim.x / tpr;
-    const int gi = threadIdx.x / tpr, eq = threadIdx.x - gi * tpr;
-    const int KnPm = KN * Pm;
-    float4 *Us = reinterpret_cast<float4 *>(red + (size_t)ng * KnPm);
-    const int64_t r0 = (int64_t)blockIdx.x * rpb, r1 = min(r0 + rpb, R);
-    float4 acc[KN];
-#pragma unroll
-    for (int k = 0; k < KN; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 *Y4 = reinterpret_cast<const float4 *>(Y) + eq;
-    // U rows of the chunk starting at rb, as this thread's share of vectors
-    auto load_u = [&](int64_t rb, float4 (&u)[UPT]) {
-        const int nr = (int)min((int64_t)CY_CH, r1 - rb);
-#pragma unroll
-        for (int q = 0; q < UPT; ++q) {
-            const int t = threadIdx.x + q * 256;
-            const int rr = t / UQ, c = t - rr * UQ;
-            u[q] = (rb < r1 && rr < nr) ? __ldg(reinterpret_cast<const float4 *>(Un + (size_t)row_id[rb + rr] * KN) + c)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-    };
-    auto store_u = [&](int buf, const float4 (&u)[UPT]) {
-#pragma unroll
-        for (int q = 0; q < UPT; ++q) {
-            const int t = threadIdx.x + q * 256;
-            if (t < CY_CH * UQ) Us[buf * CY_CH * UQ + t] = u[q];
-        }
-    };
-    float4 un[UPT];
-    load_u(r0, un);
-    store_u(0, un);
-    __syncthreads();
-    int buf = 0;
-    for (int64_t rb = r0; rb < r1; rb += CY_CH, buf ^= 1) {
-        const int nr = (int)min((int64_t)CY_CH, r1 - rb);
-        load_u(rb + CY_CH, un);  // next chunk's U rows, stored after this chunk
-        if (gi < ng) {
-            const float4 *uc = Us + buf * CY_CH * UQ;
-            const int nmine = nr > gi ? (nr - gi + ng - 1) / ng : 0;  // rows gi, gi + ng, ... of the chunk
-            float4 cur[RB], nxt[RB];
-#pragma unroll
-            for (int u = 0; u < RB; ++u)
-                cur[u] = u < nmine ? __ldg(Y4 + (size_t)(rb + gi + u * ng) * tpr) : make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int j0 = 0; j0 < nmine; j0 += RB) {
-#pragma unroll
-                for (int u = 0; u < RB; ++u) {
-                    const int jn = j0 + RB + u;
-                    nxt[u] = jn < nmine ? __ldg(Y4 + (size_t)(rb + gi + jn * ng) * tpr) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-#pragma unroll
-                for (int u = 0; u < RB; ++u) {
-                    if (j0 + u >= nmine) break;
-                    const float4 *u4 = uc + (size_t)(gi + (j0 + u) * ng) * UQ;
-#pragma unroll
-                    for (int kq = 0; kq < UQ; ++kq) {
-                        const float4 uq = u4[kq];
-                        const float uu[4] = {uq.x, uq.y, uq.z, uq.w};
-#pragma unroll
-                        for (int c = 0; c < 4; ++c) {
-                            float4 &a = acc[4 * kq + c];
-                            a.x = fmaf(uu[c], cur[u].x, a.x);
-                            a.y = fmaf(uu[c], cur[u].y, a.y);
-                            a.z = fmaf(uu[c], cur[u].z, a.z);
-                            a.w = fmaf(uu[c], cur[u].w, a.w);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < RB; ++u) cur[u] = nxt[u];
-            }
-        }
-        store_u(buf ^ 1, un);
-        __syncthreads();
-    }
-    if (gi < ng) {
-#pragma unroll
-        for (int k = 0; k < KN; ++k) reinterpret_cast<float4 *>(red + (size_t)gi * KnPm + (size_t)k * Pm)[eq] = acc[k];
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < KnPm; p += blockDim.x) {
-        float s = 0.f;
-        for (int q = 0; q < ng; ++q) s += red[(size_t)q * KnPm + p];
-        cpart[(size_t)blockIdx.x * KnPm + p] = s;
     }
 }
 
@@ -1155,97 +878,13 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     HQ_TRY(p.nm1 == 2 ? launch_hyb_nm1<2>(c, n, p, a, L) : launch_hyb_nm1<3>(c, n, p, a, L));
     HQ_TRY(prof_end(c, 3, e0));
     if (M.nspan > 0) {
-        const size_t sm = 8 * (size_t)a.Pm * sizeof(float);
+        const size_t sm = (size_t)span_fix_ns(a.Pm) * a.Pm * sizeof(float);
         HQ_CUDA(cudaFuncSetAttribute(k_span_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_span_fix<<<(unsigned)M.nspan, 256, sm, c->stream>>>(M.span, M.lrow, M.item_aux, M.ipw, c->ypart, a.Pm,
-                                                               c->Y);
+        k_span_fix<<<(unsigned)M.nspan, SF_THREADS, sm, c->stream>>>(M.span, M.lrow, M.item_aux, M.ipw, c->ypart,
+                                                                      a.Pm, c->Y);
         c->nlaunch++;
     }
     HQ_CUDA(cudaGetLastError());
-    return HOQRI_OK;
-}
-
-// A_n = Y_(n) G_(n)^T from the stored rows (Gn: G_(n) as [Kn][Pm] on the device,
-// over the padded columns when the mode's plan is padded).
-hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
-    const ModeStore &M = c->ms[n];
-    const int Kn = c->K[n];
-    FastTile pl;
-    const int Pm = hyb_tile(c, n, &pl) ? pl.Pm : (int)(c->P / Kn);
-    const int Knp = (Kn + 3) & ~3;
-    const int RT = std::min(256, 4 * (256 / (Knp / 4)));
-    const int EC = Pm < 32 ? Pm : 32;
-    const size_t smem = ((size_t)EC * (RT + 4) + (size_t)EC * Knp) * sizeof(float);
-    HQ_CUDA(cudaMemsetAsync(A_out, 0, (size_t)c->dims[n] * Kn * sizeof(float), c->stream));
-    if (M.R > 0 && (Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && (size_t)Pm * Kn * 4 <= 96 * 1024) {
-        const size_t sm2 = (size_t)Pm * Kn * sizeof(float);
-        // one wave of CTAs with equal row ranges
-#define HQ_AY(KV)                                                                                             \
-    if (Kn == KV) {                                                                                           \
-        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
-        int per_sm = 1;                                                                                       \
-        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_a_from_y2<KV>, 256, sm2));           \
-        const int g2 = (int)std::max<int64_t>(                                                                \
-            1, std::min<int64_t>(ceil_div(M.R, 2 * ay_rt<KV>()), (int64_t)c->num_sms * std::max(1, per_sm)));       \
-        const int64_t rpb2 = ceil_div(M.R, g2);                                                               \
-        k_a_from_y2<KV><<<g2, 256, sm2, c->stream>>>(c->Y, Gn, M.row_id, M.R, rpb2, Pm, A_out);             \
-    }
-        HQ_AY(4)
-        HQ_AY(8)
-        HQ_AY(16)
-        HQ_AY(32)
-#undef HQ_AY
-        c->nlaunch++;
-    } else if (M.R > 0) {
-        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, RT), (int64_t)c->num_sms * 4));
-        k_a_from_y<<<grid, 256, smem, c->stream>>>(c->Y, Gn, M.row_id, M.R, Kn, Knp, Pm, RT, A_out);
-        c->nlaunch++;
-    }
-    HQ_CUDA(cudaGetLastError());
-    return HOQRI_OK;
-}
-
-// G_(n) = U_n^T Y_(n) (Y from the last hyb_pass of mode n) into CTA partials;
-// *nblk receives the number of partials.
-hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
-    const ModeStore &M = c->ms[n];
-    const int Kn = c->K[n];
-    FastTile pl;
-    const int Pm = hyb_tile(c, n, &pl) ? pl.Pm : (int)(c->P / Kn);
-    const int Knp = (Kn + 3) & ~3;
-    const int64_t R = M.R;
-    int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),
-                                                          (int64_t)c->num_sms * 2));
-    int64_t rpb = ceil_div(std::max<int64_t>(R, 1), grid);
-    if ((Kn == 4 || Kn == 8 || Kn == 16 || Kn == 32) && Pm % 4 == 0 && Pm <= 1024 &&
-        (size_t)(256 / (Pm / 4)) * Kn * Pm * 4 + (size_t)2 * CY_CH * Kn * 4 <= 200 * 1024) {
-        const size_t sm2 = ((size_t)(256 / (Pm / 4)) * Kn * Pm + (size_t)2 * CY_CH * Kn) * sizeof(float);
-        // one wave: as many CTAs as are resident at once (at most 2 per SM)
-#define HQ_CY(KV)                                                                                                \
-    if (Kn == KV) {                                                                                              \
-        HQ_CUDA(cudaFuncSetAttribute(k_core_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
-        int per_sm = 1;                                                                                          \
-        HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_core_from_y2<KV>, 256, sm2));           \
-        grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),              \
-                                                           (int64_t)c->num_sms * std::min(2, std::max(1, per_sm)))); \
-        rpb = ceil_div(std::max<int64_t>(R, 1), grid);                                                           \
-        k_core_from_y2<KV><<<grid, 256, sm2, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Pm, rpb,    \
-                                                          (float *)c->core_part);                                \
-    }
-        HQ_CY(4)
-        HQ_CY(8)
-        HQ_CY(16)
-        HQ_CY(32)
-#undef HQ_CY
-    } else {
-        const size_t smem = (size_t)64 * Knp * sizeof(float);
-        k_core_from_y<<<grid, 256, smem, c->stream>>>(c->Y, (const float *)c->U[n], M.row_id, R, Kn, Knp, Pm, rpb,
-                                                      (float *)c->core_part);
-    }
-    c->nlaunch++;
-    HQ_CUDA(cudaGetLastError());
-    *nblk = grid;
     return HOQRI_OK;
 }
 

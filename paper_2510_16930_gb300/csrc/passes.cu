@@ -564,8 +564,18 @@ __global__ void __launch_bounds__(RED_TPB) k_core_reduce(const T *cpart, int nbl
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = RED_TPB / 32;
     const int p = blockIdx.x * 32 + lane;
     double s = 0.0;
-    if (p < P)
-        for (int b = w; b < nblk; b += nw) s += (double)cpart[(size_t)b * P + p];
+    if (p < P) {
+        // eight loads in flight, added in the same order (b = w, w + nw, ...)
+        int b = w;
+        for (; b + 7 * nw < nblk; b += 8 * nw) {
+            T x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = cpart[(size_t)(b + u * nw) * P + p];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) s += (double)x[u];
+        }
+        for (; b < nblk; b += nw) s += (double)cpart[(size_t)b * P + p];
+    }
     sh[w][lane] = s;
     __syncthreads();
     if (w == 0) {

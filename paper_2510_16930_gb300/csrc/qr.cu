@@ -166,11 +166,29 @@ __global__ void __launch_bounds__(GRAM_TPB) k_gram_df(const float *A, int64_t I,
         for (int v = 0; v < TS; ++v) h2[u][v] = l2[u][v] = 0.f;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_block;
     const int64_t r1 = min(r0 + rows_per_block, I);
+    // the rows of the next step are loaded into registers while this step's
+    // products run (LPT 16-byte vectors per thread)
+    constexpr int LPT = DF_ROWS * KC / 4 / GRAM_TPB;
+    float4 pf[LPT];
+    auto load_step = [&](int64_t rb) {
+        const int nq = rb < r1 ? (int)min((int64_t)DF_ROWS, r1 - rb) * (KC / 4) : 0;
+        const float4 *src = reinterpret_cast<const float4 *>(A + rb * KC);
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int q = t + u * GRAM_TPB;
+            pf[u] = q < nq ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load_step(r0);
     for (int64_t rb = r0; rb < r1; rb += DF_ROWS) {
         const int nr = (int)min((int64_t)DF_ROWS, r1 - rb);
         __syncthreads();
-        const float4 *src = reinterpret_cast<const float4 *>(A + rb * KC);
-        for (int q = t; q < nr * (KC / 4); q += GRAM_TPB) reinterpret_cast<float4 *>(tile)[q] = __ldg(src + q);
+#pragma unroll
+        for (int u = 0; u < LPT; ++u) {
+            const int q = t + u * GRAM_TPB;
+            if (q < nr * (KC / 4)) reinterpret_cast<float4 *>(tile)[q] = pf[u];
+        }
+        load_step(rb + DF_ROWS);
         __syncthreads();
         if (active) {
             float h1[TS][TS], l1[TS][TS];
@@ -245,6 +263,14 @@ __device__ PartSum<DF> sum_range(const void *part_v, int npairs, int p, int b0, 
         const float2 *part = static_cast<const float2 *>(part_v);
         float h4[4] = {0.f, 0.f, 0.f, 0.f}, l4[4] = {0.f, 0.f, 0.f, 0.f};
         int b = b0;
+        // eight loads in flight; partial b still goes to sum (b - b0) % 4
+        for (; b + 8 <= b1; b += 8) {
+            float2 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) x[u] = part[(size_t)(b + u) * npairs + p];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) df_add(h4[u & 3], l4[u & 3], x[u].x, x[u].y);
+        }
         for (; b + 4 <= b1; b += 4) {
             float2 x[4];
 #pragma unroll
@@ -436,6 +462,190 @@ __global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, i
     for (int t = lane; t < K * K; t += 32) {
         const int i = t / K, col = t - i * K;
         Rd[t] = i > col ? 0.0 : (i == col ? inv[i] : W[t]);
+    }
+}
+
+// ---- the Cholesky of an FP32 factor's Gram in double-float.  The Gram is
+// summed in double-float (k_gram_df), and the FP64 pipe of this GPU issues a
+// warp instruction far more slowly than the FP32 pipes, which the K dependent
+// pivot steps feel directly; so the factorisation keeps every entry as a
+// double-float pair too.  Its rounding (about 2^-46 relative per operation) is
+// below the Gram's own (a few 1e-15), and the factor is stored in FP32.
+
+// s + e = a + b exactly, for |a| >= |b| (Dekker's Fast2Sum)
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (hi, lo) = (ah + al)(bh + bl) to about 2^-46 relative: the exact product
+// ah bh = p + e by an FMA (TwoProduct), the cross terms added to e, renormalised
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &hi, float &lo) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    fast_two_sum(p, e, hi, lo);
+}
+
+// (yh, yl) = 1 / sqrt(dh + dl): the FP32 estimate y0 refined by one
+// Newton-Raphson step y = y0 + y0 r / 2 with r = 1 - d y0^2 formed in
+// double-float (y0^2 exact by TwoProduct); the step squares the estimate's
+// relative error (about 2^-22 -> 2^-44).  Outside 1e-30 < dh < 1e30 (where the
+// FP32 steps could underflow or overflow) the value comes from FP64.
+__device__ __forceinline__ void df_rsqrt(float dh, float dl, float &yh, float &yl) {
+    if (dh > 1e-30f && dh < 1e30f) {
+        const float y0 = rsqrtf(dh);
+        const float th = __fmul_rn(y0, y0);
+        const float tl = __fmaf_rn(y0, y0, -th);
+        float uh, ul;
+        df_mul(dh, dl, th, tl, uh, ul);
+        const float r = __fsub_rn(__fsub_rn(1.0f, uh), ul);  // 1 - uh is exact: uh is within 2^-21 of 1
+        fast_two_sum(y0, __fmul_rn(__fmul_rn(y0, r), 0.5f), yh, yl);
+    } else {
+        const double y = 1.0 / sqrt((double)dh + (double)dl);
+        yh = (float)y;
+        yl = (float)(y - (double)yh);
+    }
+}
+
+// W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal),
+// as double-float pairs: the same fixed order as gram_sum<true>, without the
+// final rounding to FP64.  sub: shared scratch of blockDim pairs.
+__device__ void gram_sum_df(const float2 *part, int nblk, int K, float shift, float2 *W, float2 *sub) {
+    const int npairs = K * (K + 1) / 2;
+    const int nsub = (int)blockDim.x / npairs;
+    const int t = threadIdx.x;
+    auto put = [&](int p, float hi, float lo) {
+        int rem = p, i = 0;
+        while (rem >= K - i) {
+            rem -= K - i;
+            ++i;
+        }
+        if (rem == 0) df_add(hi, lo, shift, 0.f);
+        W[i * K + i + rem] = make_float2(hi, lo);
+    };
+    if (nsub <= 1) {
+        for (int p = t; p < npairs; p += blockDim.x) {
+            const PartSum<true> r = sum_range<true>(part, npairs, p, 0, nblk);
+            put(p, r.hi, r.lo);
+        }
+        return;
+    }
+    if (t < nsub * npairs) {
+        const int p = t % npairs, q = t / npairs;
+        const int b0 = (int)((int64_t)nblk * q / nsub), b1 = (int)((int64_t)nblk * (q + 1) / nsub);
+        const PartSum<true> r = sum_range<true>(part, npairs, p, b0, b1);
+        sub[t] = make_float2(r.hi, r.lo);
+    }
+    __syncthreads();
+    for (int p = t; p < npairs; p += blockDim.x) {
+        float hi = 0.f, lo = 0.f;
+        for (int q = 0; q < nsub; ++q) df_add(hi, lo, sub[q * npairs + p].x, sub[q * npairs + p].y);
+        put(p, hi, lo);
+    }
+}
+
+// chol_warp in double-float: W = R^T R in place (pairs, R in the upper
+// triangle), inv(j) = 1 / R(j, j); the same right-looking order and lane split.
+// Returns 1 when a pivot is not above tiny_rel max_j W(j, j).
+__device__ int chol_warp_df(float2 *W, float2 *inv, const uint16_t *pairs, int K, int lane, float tiny_rel) {
+    float dmax = 0.f;
+    for (int i = 0; i < K; ++i) dmax = fmaxf(dmax, W[i * K + i].x);
+    const float tiny = tiny_rel * dmax;
+    if (!(dmax > 0.f)) return 1;
+    for (int j = 0; j < K; ++j) {
+        const float2 d = W[j * K + j];
+        if (!(d.x > tiny)) return 1;
+        float yh, yl;
+        df_rsqrt(d.x, d.y, yh, yl);
+        for (int k = j + 1 + lane; k < K; k += 32) {
+            const float2 w = W[j * K + k];
+            float h, l;
+            df_mul(w.x, w.y, yh, yl, h, l);
+            W[j * K + k] = make_float2(h, l);
+        }
+        __syncwarp();
+        const int nt = (K - j - 1) * (K - j) / 2;
+        for (int q = lane; q < nt; q += 32) {
+            const int k = pairs[q] >> 6, l = pairs[q] & 63;
+            const float2 a = W[j * K + k], b = W[j * K + l];
+            float ph, pl;
+            df_mul(a.x, a.y, b.x, b.y, ph, pl);
+            float2 w = W[k * K + l];
+            df_add(w.x, w.y, -ph, -pl);
+            W[k * K + l] = w;
+        }
+        if (lane == 0) {
+            float h, l;
+            df_mul(d.x, d.y, yh, yl, h, l);
+            W[j * K + j] = make_float2(h, l);
+            inv[j] = make_float2(yh, yl);
+        }
+        __syncwarp();
+    }
+    return 0;
+}
+
+// k_chol for double-float Gram partials (FP32 factors): the same steps,
+// decisions and output (Rd in FP64, 1 / R(j, j) on the diagonal) with the sums
+// and the factorisation in double-float.  The pivot threshold is 1e-13 of the
+// largest diagonal entry.
+__global__ void __launch_bounds__(CHOL_TPB) k_chol_df(const float2 *part, int nblk, int K, int64_t m, double *Rd,
+                                                      int32_t *flag, int pass) {
+    if (qr_skip(flag, pass)) return;
+    __shared__ float2 W[HOQRI_MAXK * HOQRI_MAXK];
+    __shared__ float2 inv[HOQRI_MAXK];
+    __shared__ float2 sub[CHOL_TPB];
+    __shared__ uint16_t pairs[HOQRI_MAXK * (HOQRI_MAXK + 1) / 2];
+    __shared__ int s_bad;
+    __shared__ float s_shift;
+    constexpr float tiny_rel = 1e-13f;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int npairs = K * (K + 1) / 2;
+    for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
+        int k = K - 1, rem = q;
+        while (rem >= K - k) {
+            rem -= K - k;
+            --k;
+        }
+        pairs[q] = (uint16_t)(k * 64 + k + rem);
+    }
+    gram_sum_df(part, nblk, K, 0.f, W, sub);
+    __syncthreads();
+    if (wid == 0) {
+        float tr = 0.f;
+        for (int i = 0; i < K; ++i) tr += W[i * K + i].x;
+        const int bad = chol_warp_df(W, inv, pairs, K, lane, tiny_rel);
+        if (lane == 0) {
+            s_bad = bad;
+            s_shift = 11.0f * ((float)m * K + (float)(K * (K + 1))) * 0x1p-53f * tr;
+        }
+    }
+    __syncthreads();
+    if (s_bad && pass == 0 && s_shift > 0.f) {
+        gram_sum_df(part, nblk, K, s_shift, W, sub);
+        __syncthreads();
+        if (wid == 0) {
+            const int bad = chol_warp_df(W, inv, pairs, K, lane, tiny_rel);
+            if (lane == 0) {
+                s_bad = bad;
+                if (!bad) flag[3] = 1;
+            }
+        }
+        __syncthreads();
+    }
+    if (s_bad) {
+        if (threadIdx.x == 0) {
+            flag[0] = 1;
+            flag[1] += 1;
+        }
+        return;
+    }
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+        const int i = t / K, col = t - i * K;
+        const float2 v = i == col ? inv[i] : W[t];
+        Rd[t] = i > col ? 0.0 : (double)v.x + (double)v.y;
     }
 }
 
@@ -655,7 +865,7 @@ void launch_gram_chol(cudaStream_t st, const T *src, int64_t I, int K, int nb, i
             }
     }
     if (df) {
-        k_chol<true><<<1, CHOL_TPB, 0, st>>>(part, nb, K, I, Rd, flag, pass);
+        k_chol_df<<<1, CHOL_TPB, 0, st>>>(static_cast<const float2 *>(part), nb, K, I, Rd, flag, pass);
     } else {
         k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, static_cast<double *>(part), flag, pass);
         k_chol<false><<<1, CHOL_TPB, 0, st>>>(part, nb, K, I, Rd, flag, pass);
