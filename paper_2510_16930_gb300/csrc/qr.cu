@@ -1,9 +1,9 @@
 // Orthonormalisation U_n <- orthonormal basis of A_n (Alg. 2, the QR step).
 //
-// CholeskyQR2 in FP64: W = A^T A (Gram, FP64 sums in a fixed order; for an
-// FP32 A double-float sums on the FP32 pipes, see k_gram_df), W = R^T R
-// (Cholesky in FP64, one CTA), A <- A R^{-1} (row-wise substitution); then
-// once more on the result.
+// CholeskyQR2: W = A^T A (Gram, FP64 sums in a fixed order; for an FP32 A
+// double-float sums on the FP32 pipes, see k_gram_df), W = R^T R (Cholesky in
+// one CTA, FP64 for an FP64 A, double-float for an FP32 A: k_chol_df),
+// A <- A R^{-1} (row-wise substitution); then once more on the result.
 // Both R factors have a positive diagonal, so the result is the Q of the thin
 // QR with diag(R) > 0.  A_n = Y_(n) G_(n)^T with G_(n) = U_n^T Y_(n) squares
 // the conditioning of Y_(n), so a first pivot that is not clearly positive is
@@ -309,45 +309,31 @@ __device__ __forceinline__ void put_pair(double *W, int K, int p, double s, doub
     W[i * K + i + rem] = rem == 0 ? s + shift : s;
 }
 
-// W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal).
-// When the pairs are fewer than the threads, the nblk partials of each pair
-// are split into nsub = blockDim / npairs contiguous block ranges, one thread
-// per (pair, range), and the nsub sums of a pair are added in range order
-// afterwards; otherwise a thread sums all partials of its pairs.  Either way
-// the order is fixed (same result every run).  DF sums are rounded to FP64
-// once, at the end.  sub: shared scratch of blockDim doubles.
-template <bool DF>
-__device__ void gram_sum(const void *part_v, int nblk, int K, double shift, double *W, double *sub) {
+// W(i, j) for i <= j = the sum of the FP64 block partials (+ shift on the
+// diagonal).  When the pairs are fewer than the threads, the nblk partials of
+// each pair are split into nsub = blockDim / npairs contiguous block ranges,
+// one thread per (pair, range), and the nsub sums of a pair are added in range
+// order afterwards; otherwise a thread sums all partials of its pairs.  Either
+// way the order is fixed (same result every run).  sub: shared scratch of
+// blockDim doubles.
+__device__ void gram_sum(const double *part, int nblk, int K, double shift, double *W, double *sub) {
     const int npairs = K * (K + 1) / 2;
     const int nsub = (int)blockDim.x / npairs;
     const int t = threadIdx.x;
     if (nsub <= 1) {
-        for (int p = t; p < npairs; p += blockDim.x) {
-            const PartSum<DF> r = sum_range<DF>(part_v, npairs, p, 0, nblk);
-            put_pair(W, K, p, DF ? (double)r.hi + (double)r.lo : r.d, shift);
-        }
+        for (int p = t; p < npairs; p += blockDim.x)
+            put_pair(W, K, p, sum_range<false>(part, npairs, p, 0, nblk).d, shift);
         return;
     }
     if (t < nsub * npairs) {
         const int p = t % npairs, q = t / npairs;
         const int b0 = (int)((int64_t)nblk * q / nsub), b1 = (int)((int64_t)nblk * (q + 1) / nsub);
-        const PartSum<DF> r = sum_range<DF>(part_v, npairs, p, b0, b1);
-        if constexpr (DF)
-            reinterpret_cast<float2 *>(sub)[t] = make_float2(r.hi, r.lo);
-        else
-            sub[t] = r.d;
+        sub[t] = sum_range<false>(part, npairs, p, b0, b1).d;
     }
     __syncthreads();
     for (int p = t; p < npairs; p += blockDim.x) {
         double s = 0.0;
-        if constexpr (DF) {
-            const float2 *sb = reinterpret_cast<const float2 *>(sub);
-            float hi = 0.f, lo = 0.f;
-            for (int q = 0; q < nsub; ++q) df_add(hi, lo, sb[q * npairs + p].x, sb[q * npairs + p].y);
-            s = (double)hi + (double)lo;
-        } else {
-            for (int q = 0; q < nsub; ++q) s += sub[q * npairs + p];
-        }
+        for (int q = 0; q < nsub; ++q) s += sub[q * npairs + p];
         put_pair(W, K, p, s, shift);
     }
 }
@@ -395,17 +381,15 @@ __device__ int chol_warp(double *W, double *inv, const uint16_t *pairs, int K, i
     return 0;
 }
 
-// Sum of the Gram partials, Cholesky W = R^T R (of W + s I after a breakdown in
-// the first pass).  Rd receives R with 1 / R(j, j) on its diagonal and zeros
-// below it, the form the row substitution of the apply step reads.  The
-// partial sums use all threads; the factorisation runs in warp 0.  m = rows
-// of A.  A pivot counts as not clearly positive below 1e-14 of the largest
-// diagonal entry for FP64 sums and below 1e-13 for double-float ones (whose
-// rounding error is up to ten times larger).  The double-float (FP32 data)
-// form refines the reciprocal square root by one Newton-Raphson step (about
-// 2e-14 relative: the factor is stored in FP32), the FP64 form by two.
-template <bool DF>
-__global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, int K, int64_t m, double *Rd,
+// Sum of the FP64 Gram partials, Cholesky W = R^T R in FP64 (of W + s I after
+// a breakdown in the first pass).  Rd receives R with 1 / R(j, j) on its
+// diagonal and zeros below it, the form the row substitution of the apply step
+// reads.  The partial sums use all threads; the factorisation runs in warp 0.
+// m = rows of A.  A pivot counts as not clearly positive below 1e-14 of the
+// largest diagonal entry; the reciprocal square root takes two Newton-Raphson
+// steps from the FP32 estimate.  (Double-float partials of FP32 factors go to
+// k_chol_df.)
+__global__ void __launch_bounds__(CHOL_TPB) k_chol(const double *part, int nblk, int K, int64_t m, double *Rd,
                                                    int32_t *flag, int pass) {
     if (qr_skip(flag, pass)) return;
     __shared__ double W[HOQRI_MAXK * HOQRI_MAXK];
@@ -414,8 +398,8 @@ __global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, i
     __shared__ uint16_t pairs[HOQRI_MAXK * (HOQRI_MAXK + 1) / 2];
     __shared__ int s_bad;
     __shared__ double s_shift;
-    constexpr double tiny_rel = DF ? 1e-13 : 1e-14;
-    constexpr int NR = DF ? 1 : 2;
+    constexpr double tiny_rel = 1e-14;
+    constexpr int NR = 2;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int npairs = K * (K + 1) / 2;
     for (int q = threadIdx.x; q < npairs; q += blockDim.x) {
@@ -427,7 +411,7 @@ __global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, i
         }
         pairs[q] = (uint16_t)(k * 64 + k + rem);
     }
-    gram_sum<DF>(part, nblk, K, 0.0, W, sub);
+    gram_sum(part, nblk, K, 0.0, W, sub);
     __syncthreads();
     if (wid == 0) {
         double tr = 0.0;
@@ -440,7 +424,7 @@ __global__ void __launch_bounds__(CHOL_TPB) k_chol(const void *part, int nblk, i
     }
     __syncthreads();
     if (s_bad && pass == 0 && s_shift > 0.0) {
-        gram_sum<DF>(part, nblk, K, s_shift, W, sub);
+        gram_sum(part, nblk, K, s_shift, W, sub);
         __syncthreads();
         if (wid == 0) {
             const int bad = chol_warp<NR>(W, inv, pairs, K, lane, tiny_rel);
@@ -510,8 +494,7 @@ __device__ __forceinline__ void df_rsqrt(float dh, float dl, float &yh, float &y
 }
 
 // W(i, j) for i <= j = the sum of the block partials (+ shift on the diagonal),
-// as double-float pairs: the same fixed order as gram_sum<true>, without the
-// final rounding to FP64.  sub: shared scratch of blockDim pairs.
+// as double-float pairs, summed in a fixed order.  sub: shared scratch of blockDim pairs.
 __device__ void gram_sum_df(const float2 *part, int nblk, int K, float shift, float2 *W, float2 *sub) {
     const int npairs = K * (K + 1) / 2;
     const int nsub = (int)blockDim.x / npairs;
@@ -868,7 +851,7 @@ void launch_gram_chol(cudaStream_t st, const T *src, int64_t I, int K, int nb, i
         k_chol_df<<<1, CHOL_TPB, 0, st>>>(static_cast<const float2 *>(part), nb, K, I, Rd, flag, pass);
     } else {
         k_gram_partial<T><<<nb, GRAM_TPB, 0, st>>>(src, I, K, rpb, static_cast<double *>(part), flag, pass);
-        k_chol<false><<<1, CHOL_TPB, 0, st>>>(part, nb, K, I, Rd, flag, pass);
+        k_chol<<<1, CHOL_TPB, 0, st>>>(static_cast<const double *>(part), nb, K, I, Rd, flag, pass);
     }
 }
 
