@@ -328,6 +328,16 @@ HOQRI_API hoqri_status hoqri_server_take(hoqri_server *srv, int64_t id, void *co
 /* Frees every request and the server; NULL is a no-op. */
 HOQRI_API void hoqri_server_destroy(hoqri_server *srv);
 
+/*
+ * Contexts created on a stream (not the legacy default stream) allocate from a
+ * memory pool per device owned by the library, which keeps the memory of
+ * destroyed contexts reserved for the next ones (no mapping and unmapping per
+ * context).  This call releases the reserved memory of every such pool to the
+ * device; memory of live contexts stays allocated.  Thread safe; always
+ * HOQRI_OK.
+ */
+HOQRI_API hoqri_status hoqri_trim_memory(void);
+
 /* Message for the calling thread's last failed call ("" if none). */
 HOQRI_API const char *hoqri_last_error(void);
 

@@ -222,7 +222,7 @@ hoqri_status build_fiber(hoqri_ctx *c, int n) {
     // holds at least one piece
     int per_sm = 1;
     const size_t smem = fib_smem(s);
-    HQ_CUDA(cudaFuncSetAttribute(s.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HQ_CUDA(smem_limit(s.fn, smem));
     HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, s.fn, FB_WARPS * 32, smem));
     per_sm = std::max(1, per_sm);
     int W = 0;

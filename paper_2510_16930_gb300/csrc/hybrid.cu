@@ -716,8 +716,8 @@ hoqri_status launch_hyb_nm1(hoqri_ctx *c, int n, const FastTile &p, HybArgs &a, 
     if (p.TL == TLV && p.TV == TVV && L.MT == MTV && L.NT == NTV) {                                          \
         auto k0 = k_hyb<NM1, TLV, TVV, MTV, NTV, 0>;                                                         \
         auto k1 = k_hyb<NM1, TLV, TVV, 0, 0, 1>;                                                             \
-        HQ_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
-        HQ_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));        \
+        HQ_CUDA(smem_limit(k0, L.smem));        \
+        HQ_CUDA(smem_limit(k1, L.smem));        \
         HQ_CUDA(cudaFuncSetAttribute(k0, cudaFuncAttributePreferredSharedMemoryCarveout, carve));           \
         HQ_CUDA(cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, carve));           \
         if (a.nitem_long > 0) {                                                                              \
@@ -879,7 +879,7 @@ hoqri_status hyb_pass(hoqri_ctx *c, int n) {
     HQ_TRY(prof_end(c, 3, e0));
     if (M.nspan > 0) {
         const size_t sm = (size_t)span_fix_ns(a.Pm) * a.Pm * sizeof(float);
-        HQ_CUDA(cudaFuncSetAttribute(k_span_fix, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        HQ_CUDA(smem_limit(k_span_fix, sm));
         k_span_fix<<<(unsigned)M.nspan, SF_THREADS, sm, c->stream>>>(M.span, M.lrow, M.item_aux, M.ipw, c->ypart,
                                                                       a.Pm, c->Y);
         c->nlaunch++;

@@ -202,6 +202,16 @@ cudaError_t raw_alloc(void **p, size_t bytes, cudaStream_t st);
 void raw_free(void *p, cudaStream_t st);
 hoqri_status dalloc(hoqri_ctx *c, void **p, size_t bytes);
 void dfree(void *p, cudaStream_t st = nullptr);
+// Lets a kernel take `bytes` of dynamic shared memory on the current device by
+// setting its limit to the most it may have (an error if `bytes` exceeds that).
+// Contexts are built on several host threads at once (the request server):
+// with the limit set to each launch's own need, a limit lowered by one thread
+// between another thread's setting and its launch would fail that launch.
+cudaError_t smem_limit_raw(const void *fn, size_t bytes);
+template <typename F>
+cudaError_t smem_limit(F *fn, size_t bytes) {
+    return smem_limit_raw(reinterpret_cast<const void *>(fn), bytes);
+}
 
 // setup (setup.cu)
 hoqri_status build_storage(hoqri_ctx *c, const int32_t *const *idx_dev, const void *vals_dev, int64_t nnz_raw);

@@ -759,7 +759,7 @@ hoqri_status launch_generic(hoqri_ctx *c, PassArgs<T> &a, int grid, size_t smem,
 #define HQ_GEN(PLV)                                                                                   \
     case PLV: {                                                                                       \
         auto kern = k_pass_generic<T, PLV, CORE>;                                                     \
-        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)); \
+        HQ_CUDA(smem_limit(kern, smem)); \
         kern<<<grid, GEN_WARPS * 32, smem, c->stream>>>(a);                                           \
         c->nlaunch++;                                                                                 \
         break;                                                                                        \
@@ -813,7 +813,7 @@ hoqri_status launch_fast_nm1(hoqri_ctx *c, const FastTile &p, FastArgs &a, const
 #define HQ_FAST(TLV, TVV)                                                                                  \
     if (p.TL == TLV && p.TV == TVV) {                                                                      \
         auto kern = k_pass_fast<NM1, TLV, TVV, CORE>;                                                      \
-        HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));    \
+        HQ_CUDA(smem_limit(kern, L.smem));    \
         int per_sm = 0;                                                                                    \
         HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L.warps * 32, L.smem));      \
         per_sm = std::max(1, std::min(per_sm, FAST_MAX_CTAS_PER_SM));                                      \

@@ -99,6 +99,34 @@ __global__ void k_coalesce_values(IdxPack idx, IdxPackW cidx, int N, const int32
     }
 }
 
+// bit layout of the packed lexicographic key: mode m at bits [shift[m], shift[m] + bits[m])
+struct KeyLayout {
+    int32_t shift[HOQRI_MAXN];
+    int32_t bits[HOQRI_MAXN];
+};
+
+// head[s] = 1 if sorted position s starts a new coordinate (equal packed keys are equal coordinates)
+__global__ void k_heads_keys(const uint64_t *keys, int64_t n, int32_t *head) {
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n; s += (int64_t)gridDim.x * blockDim.x)
+        head[s] = (s == 0) || (keys[s] != keys[s - 1]);
+}
+
+// one coordinate per run of equal sorted keys: its value is the FP64 sum of the
+// run's values in sorted (= input, the sort is stable) order, its indices are
+// unpacked from the key
+template <typename T>
+__global__ void k_coalesce_sorted(const uint64_t *keys, const T *svals, KeyLayout kl, IdxPackW cidx, int N,
+                                  const int64_t *run_start, int64_t nu, int64_t n, T *cval) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu; u += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = run_start[u], b = (u + 1 < nu) ? run_start[u + 1] : n;
+        double s = 0.0;
+        for (int64_t q = a; q < b; ++q) s += (double)svals[q];
+        cval[u] = (T)s;
+        const uint64_t k = keys[a];
+        for (int m = 0; m < N; ++m) cidx.p[m][u] = (int32_t)((k >> kl.shift[m]) & ((1ull << kl.bits[m]) - 1));
+    }
+}
+
 // deterministic FP64 sum of squares: fixed grid, fixed per-thread stride, tree in shared memory
 template <typename T>
 __global__ void k_sumsq_partial(const T *v, int64_t n, double *part) {
@@ -168,12 +196,21 @@ __global__ void k_hyb_gather(IdxPack src, IdxPackW dst, int nm1, const int32_t *
     }
 }
 
-// map of the long part: position lrp[j] + q holds sorted position row_ptr[lrow[j]] + q
+// map of the long part: position lrp[j] + q holds sorted position row_ptr[lrow[j]] + q;
+// a thread per position finds its row j by binary search over lrp (Zipf rows
+// differ in length by orders of magnitude, so a block per row would leave
+// one block with most of the work)
 __global__ void k_map_long(const int64_t *lrp, const int32_t *lrow, const int64_t *row_ptr, int64_t nlong,
                            int32_t *map) {
-    for (int64_t j = blockIdx.x; j < nlong; j += gridDim.x) {
-        const int64_t a = lrp[j], len = lrp[j + 1] - a, s = row_ptr[lrow[j]];
-        for (int64_t q = threadIdx.x; q < len; q += blockDim.x) map[a + q] = (int32_t)(s + q);
+    const int64_t total = lrp[nlong];
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nlong - 1;  // last j with lrp[j] <= p
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (lrp[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        map[p] = (int32_t)(row_ptr[lrow[lo]] + (p - lrp[lo]));
     }
 }
 
@@ -247,34 +284,44 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
         return HOQRI_ERR_INVALID;
     }
 
-    // ---- 2. lexicographic stable sort of the raw coordinates
-    int32_t *perm_a, *perm_b;
-    HQ_TRY(tmp.get(&perm_a, nnz_raw));
-    HQ_TRY(tmp.get(&perm_b, nnz_raw));
-    int32_t *perm = perm_a;
+    // ---- 2. lexicographic stable sort of the raw coordinates.  When the packed
+    // coordinate fits 64 bits the (key, value) pairs are sorted together: equal
+    // coordinates become adjacent with their values in input order, and the
+    // coordinates are unpacked from the keys (no gathers through a permutation).
+    // Otherwise a permutation is sorted mode by mode (least significant first,
+    // stable passes give lexicographic order) and gathered through.
     int total_bits = 0;
-    int32_t shift[HOQRI_MAXN];
+    KeyLayout kl{};
     for (int m = N - 1; m >= 0; --m) {
-        shift[m] = total_bits;
-        total_bits += bits_for(c->dims[m]);
+        kl.shift[m] = total_bits;
+        kl.bits[m] = bits_for(c->dims[m]);
+        total_bits += kl.bits[m];
     }
+    const bool packed = total_bits <= 64;
     const int nn = (int)nnz_raw;
-    if (nnz_raw > 0 && total_bits <= 64) {
-        uint64_t *ka, *kb;
-        int32_t *shift_dev;
+    int32_t *perm = nullptr;
+    uint64_t *skeys = nullptr;
+    T *svals = nullptr;
+    if (nnz_raw > 0 && packed) {
+        uint64_t *ka;
+        int32_t *shift_dev, *unused;
         HQ_TRY(tmp.get(&ka, nnz_raw));
-        HQ_TRY(tmp.get(&kb, nnz_raw));
+        HQ_TRY(tmp.get(&skeys, nnz_raw));
+        HQ_TRY(tmp.get(&svals, nnz_raw));
+        HQ_TRY(tmp.get(&unused, nnz_raw));
         HQ_TRY(tmp.get(&shift_dev, N));
-        HQ_CUDA(cudaMemcpyAsync(shift_dev, shift, N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-        k_pack_keys<<<G, TPB, 0, st>>>(in, N, nnz_raw, shift_dev, ka, perm_a);
+        HQ_CUDA(cudaMemcpyAsync(shift_dev, kl.shift, N * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+        k_pack_keys<<<G, TPB, 0, st>>>(in, N, nnz_raw, shift_dev, ka, unused);
         size_t tb = 0;
-        HQ_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, ka, kb, perm_a, perm_b, nn, 0, total_bits, st));
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, ka, skeys, (const T *)vals_dev, svals, nn, 0, total_bits,
+                                                st));
         char *t;
         HQ_TRY(tmp.get(&t, tb));
-        HQ_CUDA(cub::DeviceRadixSort::SortPairs(t, tb, ka, kb, perm_a, perm_b, nn, 0, total_bits, st));
-        perm = perm_b;
+        HQ_CUDA(cub::DeviceRadixSort::SortPairs(t, tb, ka, skeys, (const T *)vals_dev, svals, nn, 0, total_bits, st));
     } else if (nnz_raw > 0) {
-        // least significant mode first; stable passes give lexicographic order
+        int32_t *perm_a, *perm_b;
+        HQ_TRY(tmp.get(&perm_a, nnz_raw));
+        HQ_TRY(tmp.get(&perm_b, nnz_raw));
         uint32_t *ka, *kb;
         HQ_TRY(tmp.get(&ka, nnz_raw));
         HQ_TRY(tmp.get(&kb, nnz_raw));
@@ -298,7 +345,8 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
     HQ_TRY(tmp.get(&incl, nnz_raw));
     int64_t nu = 0;
     if (nnz_raw > 0) {
-        k_heads<<<G, TPB, 0, st>>>(in, N, perm, nnz_raw, head);
+        if (packed) k_heads_keys<<<G, TPB, 0, st>>>(skeys, nnz_raw, head);
+        else k_heads<<<G, TPB, 0, st>>>(in, N, perm, nnz_raw, head);
         size_t tb = 0;
         HQ_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tb, head, incl, nn, st));
         char *t;
@@ -319,8 +367,12 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
     HQ_TRY(tmp.get(&cval, nu));
     if (nu > 0) {
         k_run_starts<<<G, TPB, 0, st>>>(head, incl, nnz_raw, run_start);
-        k_coalesce_values<T><<<std::min(grid_for(nu), c->num_sms * 8), TPB, 0, st>>>(
-            in, cidx, N, perm, run_start, nu, nnz_raw, (const T *)vals_dev, cval);
+        const int Gc = std::min(grid_for(nu), c->num_sms * 8);
+        if (packed)
+            k_coalesce_sorted<T><<<Gc, TPB, 0, st>>>(skeys, svals, kl, cidx, N, run_start, nu, nnz_raw, cval);
+        else
+            k_coalesce_values<T><<<Gc, TPB, 0, st>>>(in, cidx, N, perm, run_start, nu, nnz_raw, (const T *)vals_dev,
+                                                     cval);
     }
 
     // ---- 3. ||X||^2
@@ -364,12 +416,22 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
             ow.p[j] = M.oidx[j];
         }
         int64_t R = 0;
-        if (nu > 0) {
+        // the coalesced coordinates are in lexicographic order with mode 0 most
+        // significant, so the stable sort by i_0 is the identity: mode 0 copies
+        const uint32_t *skey = n == 0 ? reinterpret_cast<const uint32_t *>(cidx.p[0]) : kb;
+        if (nu > 0 && n == 0) {
+            k_iota<<<Gu, TPB, 0, st>>>(M.perm, nu);
+            for (int m = 1; m < N; ++m)
+                HQ_CUDA(cudaMemcpyAsync(ow.p[m - 1], cidx.p[m], nu * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+            HQ_CUDA(cudaMemcpyAsync(M.vals, cval, nu * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        } else if (nu > 0) {
             HQ_CUDA(cudaMemcpyAsync(ka, cidx.p[n], nu * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
             k_iota<<<Gu, TPB, 0, st>>>(ia, nu);
             HQ_CUDA(cub::DeviceRadixSort::SortPairs(tsort, tb_sort, ka, kb, ia, M.perm, nun, 0, bits_for(c->dims[n]), st));
             k_gather_mode<T><<<Gu, TPB, 0, st>>>(cin, ow, N, n, M.perm, nu, cval, (T *)M.vals);
-            k_row_heads<<<Gu, TPB, 0, st>>>(kb, nu, rhead);
+        }
+        if (nu > 0) {
+            k_row_heads<<<Gu, TPB, 0, st>>>(skey, nu, rhead);
             HQ_CUDA(cub::DeviceScan::InclusiveSum(tscan, tb_scan, rhead, rincl, nun, st));
             int32_t Rh = 0;
             HQ_CUDA(cudaMemcpyAsync(&Rh, rincl + nu - 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -379,7 +441,7 @@ static hoqri_status build_storage_t(hoqri_ctx *c, const int32_t *const *idx_dev,
         M.R = R;
         HQ_TRY(dalloc(c, (void **)&M.row_id, std::max<int64_t>(R, 1) * sizeof(int32_t)));
         HQ_TRY(dalloc(c, (void **)&M.row_ptr, (R + 1) * sizeof(int64_t)));
-        if (nu > 0) k_row_desc<<<Gu, TPB, 0, st>>>(kb, rhead, rincl, nu, M.row_id, M.row_ptr);
+        if (nu > 0) k_row_desc<<<Gu, TPB, 0, st>>>(skey, rhead, rincl, nu, M.row_id, M.row_ptr);
         k_set_last<<<1, 1, 0, st>>>(M.row_ptr, R, nu);
     }
     HQ_CUDA(cudaGetLastError());
@@ -466,12 +528,20 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     HQ_CUDA(cudaMemcpyAsync(rp.data(), M.row_ptr, (M.R + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     HQ_CUDA(cudaStreamSynchronize(st));
     std::vector<int32_t> lrow, srt;
+    // short rows by length, longest first, ties in row order (a counting sort:
+    // lengths are at most Lshort)
+    std::vector<int64_t> nlen(Lshort + 2, 0);
     for (int64_t r = 0; r < M.R; ++r) {
-        if (rp[r + 1] - rp[r] > Lshort) lrow.push_back((int32_t)r);
-        else srt.push_back((int32_t)r);
+        const int64_t len = rp[r + 1] - rp[r];
+        if (len > Lshort) lrow.push_back((int32_t)r);
+        else ++nlen[Lshort - len + 1];
     }
-    std::stable_sort(srt.begin(), srt.end(),
-                     [&](int32_t a, int32_t b) { return (rp[a + 1] - rp[a]) > (rp[b + 1] - rp[b]); });
+    for (int64_t l = 1; l <= Lshort + 1; ++l) nlen[l] += nlen[l - 1];
+    srt.resize((size_t)nlen[Lshort + 1]);
+    for (int64_t r = 0; r < M.R; ++r) {
+        const int64_t len = rp[r + 1] - rp[r];
+        if (len <= Lshort) srt[(size_t)nlen[Lshort - len]++] = (int32_t)r;
+    }
     const int64_t nlong = (int64_t)lrow.size();
     std::vector<int64_t> lrp(nlong + 1, 0);
     for (int64_t j = 0; j < nlong; ++j) lrp[j + 1] = lrp[j] + (rp[lrow[j] + 1] - rp[lrow[j]]);
@@ -567,7 +637,8 @@ static hoqri_status build_hybrid_t(hoqri_ctx *c, int n, int64_t Lshort, int64_t 
     HQ_TRY(tmp.get(&dmap, total + 16));
     HQ_CUDA(cudaMemsetAsync(dmap, 0xFF, (total + 16) * sizeof(int32_t), st));
     if (nlong > 0)
-        k_map_long<<<(unsigned)std::min<int64_t>(nlong, 65535), TPB, 0, st>>>(M.lrp, M.lrow, M.row_ptr, nlong, dmap);
+        k_map_long<<<std::min(grid_for(total_long), c->num_sms * 8), TPB, 0, st>>>(M.lrp, M.lrow, M.row_ptr, nlong,
+                                                                                   dmap);
     if (nslice > 0)
         k_map_slices<<<(unsigned)std::min<int64_t>(nslice, 1 << 20), 64, 0, st>>>(M.sbase, M.srow, M.row_ptr, nslice,
                                                                                  SW, dmap);

@@ -425,7 +425,7 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
 #define HQ_AY(KV)                                                                                              \
     if (Kn == KV) {                                                                                            \
         const size_t sm2 = ((size_t)Pm * KV + (size_t)AY_NS * ay_rb<KV>() * AY_LD) * sizeof(float);            \
-        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2)); \
+        HQ_CUDA(smem_limit(k_a_from_y2<KV>, sm2)); \
         int per_sm = 1;                                                                                        \
         HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_a_from_y2<KV>, 256, sm2));            \
         const int g2 = (int)std::max<int64_t>(                                                                 \
@@ -440,7 +440,7 @@ hoqri_status hyb_a_from_y(hoqri_ctx *c, int n, const float *Gn, float *A_out) {
 #undef HQ_AY
         c->nlaunch++;
     } else if (M.R > 0) {
-        HQ_CUDA(cudaFuncSetAttribute(k_a_from_y, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        HQ_CUDA(smem_limit(k_a_from_y, smem));
         const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(M.R, RT), (int64_t)c->num_sms * 4));
         k_a_from_y<<<grid, 256, smem, c->stream>>>(c->Y, Gn, M.row_id, M.R, Kn, Knp, Pm, RT, A_out);
         c->nlaunch++;
@@ -470,7 +470,7 @@ hoqri_status hyb_core_partials(hoqri_ctx *c, int n, int *nblk) {
         // one wave: as many CTAs as are resident at once (at most 2 per SM)
 #define HQ_CY(KV)                                                                                                    \
     if (Kn == KV) {                                                                                                  \
-        HQ_CUDA(cudaFuncSetAttribute(k_core_from_y2<KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cy_smem)); \
+        HQ_CUDA(smem_limit(k_core_from_y2<KV>, cy_smem)); \
         int per_sm = 1;                                                                                              \
         HQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_core_from_y2<KV>, 256, cy_smem));           \
         grid = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(R, 1), 256),                  \

@@ -25,8 +25,8 @@ _STATUS = {0: "HOQRI_OK", 1: "HOQRI_ERR_INVALID", 2: "HOQRI_ERR_OOM", 3: "HOQRI_
 SYMBOLS = ("hoqri_default_options", "hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize",
            "hoqri_iterate", "hoqri_run", "hoqri_grad_norm2", "hoqri_init_hosvd",
            "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_layout",
-           "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_last_error",
-           "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
+           "hoqri_profile_enable", "hoqri_profile_read", "hoqri_synchronize", "hoqri_trim_memory",
+           "hoqri_last_error", "hoqri_destroy", "hoqri_orthonormalize_noalloc", "hoqri_server_create", "hoqri_server_submit",
            "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take", "hoqri_server_destroy")
 HOQRI_REQ_QUEUED, HOQRI_REQ_RUNNING, HOQRI_REQ_DONE, HOQRI_REQ_FAILED = range(4)
 
@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
     L.hoqri_profile_enable.argtypes = [vp, i32]
     L.hoqri_profile_read.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(i64)]
     L.hoqri_synchronize.argtypes = [vp]
+    L.hoqri_trim_memory.argtypes = []
     L.hoqri_last_error.restype = C.c_char_p
     L.hoqri_orthonormalize_noalloc.argtypes = [i32, i64, i32, vp, vp, vp]
     L.hoqri_server_create.argtypes = [C.POINTER(vp), i64, i32]
@@ -100,7 +101,7 @@ def load(build_if_missing: bool = True):
     for name in ("hoqri_create", "hoqri_core", "hoqri_ttmctc", "hoqri_orthonormalize", "hoqri_iterate", "hoqri_run",
                  "hoqri_grad_norm2", "hoqri_init_hosvd",
                  "hoqri_get_factor", "hoqri_set_factor", "hoqri_fit", "hoqri_info", "hoqri_layout", "hoqri_synchronize",
-                 "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
+                 "hoqri_trim_memory", "hoqri_profile_enable", "hoqri_profile_read", "hoqri_orthonormalize_noalloc", "hoqri_server_create",
                  "hoqri_server_submit", "hoqri_server_step", "hoqri_server_poll", "hoqri_server_take"):
         getattr(L, name).restype = C.c_int
     _lib = L
@@ -241,6 +242,11 @@ def hoqri_profile_read(ctx):
 
 def hoqri_synchronize(ctx):
     _check(load().hoqri_synchronize(ctx))
+
+
+def hoqri_trim_memory():
+    """Releases the device memory the library's pools keep for new contexts."""
+    _check(load().hoqri_trim_memory())
 
 
 def hoqri_last_error() -> str:
