@@ -245,6 +245,14 @@ def cpu_oracle_rate(X, U0, target_s, max_sample=None):
     if max_sample:
         S = min(S, max_sample)
     t = run(S) if S != S2 else t2
+    # the calibration runs are short enough that the sweep's fixed part (the QR
+    # of every factor) can inflate the slope: if the sample ran well short of
+    # the target, scale it up once from its own time
+    if t < 0.5 * target_s and S < X.nnz and not (max_sample and S >= max_sample):
+        S = int(min(X.nnz, 4 * S, S * target_s / max(t, 1e-3)))
+        if max_sample:
+            S = min(S, max_sample)
+        t = run(S)
     return S * N / t, oracle.threads(), f"first {S} of {X.nnz} nonzeros, one sweep (N={N} modes), FP64", t
 
 

@@ -1,7 +1,7 @@
 // One-stream-per-mode TTMcTC for FP32 on the hybrid layout.
 //
 // For mode n the pass forms every row y_i of Y_(n) = (X x_{-n} {U^T})_(n) once
-// (Eq. ttmctc, Y is "the mode-n matricization of X x_{-n} {U^T}"), writes
+// (Eq. ttmctc: Y_(n) unfolds the product of X with U_m^T along every mode m != n), writes
 //   A_n(i, :) = G_(n) y_i      (the TTMcTC output, Eq. ttmctc)
 // and stores y_i in a dense R_n x P_{-n} buffer.  After the QR of A_n the core
 // for the next block update is the dense product
