@@ -668,11 +668,15 @@ def run_ours(args):
         legs.discard("serve")
     rank, world, local = dist_info()
     side = rank == 0 and world == 1
-    # workloads of the later legs are drawn by a process pool while the main
-    # workload runs (spawn processes: safe to start before CUDA is initialised)
+    # workloads of the later legs are drawn by a process pool (spawn processes)
+    # started after the end-to-end timing, so that timing sees a quiet host
     pool = None
     pending = {}
-    if side and legs & {"c3", "c4", "serve"}:
+
+    def start_pool():
+        nonlocal pool
+        if not (side and legs & {"c3", "c4", "serve"}) or pool is not None:
+            return
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(processes=max(2, min(16, (os.cpu_count() or 4) - 2)))
         for name in ("c3", "c4"):
@@ -795,6 +799,7 @@ def run_ours(args):
                               f"factors and fit to host",
                       "s_per_step": t_e2e}
         del idx_h, vals_h, U0_h, U_h
+    start_pool()
     orc = None
     if side and legs & {"forms", "c3", "sweeps"}:
         from oracle import oracle as orc
