@@ -131,7 +131,8 @@ def test_fit_and_nnz_after_coalescing(orc):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-@pytest.mark.parametrize("I,K", [(1000, 5), (257, 16), (64, 64), (5000, 8), (16, 1)])
+@pytest.mark.parametrize("I,K", [(1000, 5), (257, 16), (64, 64), (5000, 8), (16, 1), (3001, 10), (2000, 12),
+                                 (4000, 20), (1500, 24)])
 def test_orthonormalize_matches_householder(orc, I, K, prec):
     rng = np.random.default_rng(I + K)
     A = rng.standard_normal((I, K)) * np.logspace(0, -2, K)[None, :]
@@ -148,9 +149,10 @@ def test_orthonormalize_matches_householder(orc, I, K, prec):
 
 
 @pytest.mark.parametrize("prec", [FP64, FP32])
-def test_orthonormalize_rank_deficient_falls_back(orc, prec):
+@pytest.mark.parametrize("K", [6, 10])
+def test_orthonormalize_rank_deficient_falls_back(orc, prec, K):
     rng = np.random.default_rng(8)
-    I, K = 300, 6
+    I = 300
     A = rng.standard_normal((I, K))
     A[:, 3] = 0.0
     A[:, 5] = A[:, 1]
@@ -179,14 +181,15 @@ def _ill_conditioned(kind, I, K, seed):
     return (Q0 * sig[None, :]) @ V.T
 
 
-@pytest.mark.parametrize("prec,kind", [(FP64, "scaled"), (FP32, "scaled"), (FP64, "graded")])
-def test_orthonormalize_ill_conditioned_is_shifted_not_broken(orc, prec, kind):
+@pytest.mark.parametrize("prec,kind,K", [(FP64, "scaled", 16), (FP32, "scaled", 16), (FP64, "graded", 16),
+                                        (FP32, "scaled", 10), (FP32, "scaled", 20)])
+def test_orthonormalize_ill_conditioned_is_shifted_not_broken(orc, prec, kind, K):
     """Unshifted CholeskyQR2 breaks down on these inputs; with qr_kind 2 (a
     breakdown is an error) the call succeeds, so the shifted first pass
     (shifted CholeskyQR3) produced Q.  Q is orthonormal, spans A, and equals the
     oracle's Q to the conditioning of the problem (kappa u ~ 1e-7 for the graded
     case)."""
-    I, K = 5000, 16
+    I = 5000
     A = _ill_conditioned(kind, I, K, 31)
     npdt = np.float64 if prec == FP64 else np.float32
     A = A.astype(npdt)
