@@ -21,6 +21,9 @@ object per further leg (each can be skipped with --legs):
   serve    the serving stream (Poisson arrivals of the request mix) through
            the request server against the same requests run one after another
            as plain contexts;
+  serve_full (not in the default list) the same on the first --serve-full-requests
+           requests of the mix without the P_{-n} <= 2048 redraw, whose large
+           cores run on the column-blocked two-pass kernels;
   autotune the autotuner (lane tile, long-row threshold, work-item size) against
            the default layout on the main workload, per mode;
   hosvd    the HOSVD start on the main workload.
@@ -71,6 +74,8 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true", help="skip the precision legs (forms, c3, c4)")
     ap.add_argument("--legs", default="forms,autotune,c3,c4,sweeps,serve,hosvd",
                     help="comma list of the legs to run after the main measurement")
+    ap.add_argument("--serve-full-requests", type=int, default=100,
+                    help="requests of the serve_full leg (the unrestricted mix)")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving mix to stream through the server (0: skip)")
     ap.add_argument("--one-stream", type=int, default=0, help="hoqri_options.one_stream of the main workload")
@@ -675,7 +680,7 @@ def run_ours(args):
 
     def start_pool():
         nonlocal pool
-        if not (side and legs & {"c3", "c4", "serve"}) or pool is not None:
+        if not (side and legs & {"c3", "c4", "serve", "serve_full"}) or pool is not None:
             return
         import multiprocessing as mp
         pool = mp.get_context("spawn").Pool(processes=max(2, min(16, (os.cpu_count() or 4) - 2)))
@@ -686,6 +691,10 @@ def run_ours(args):
             from paper_2510_16930_gb300 import serve as serve_mod
             pending["serve"] = serve_mod.draw_requests_async(pool, args.serve_requests, serve_mod.SERVE_SEED,
                                                              max_pm=SERVE_MAX_PM)
+        if "serve_full" in legs:
+            from paper_2510_16930_gb300 import serve as serve_mod
+            pending["serve_full"] = serve_mod.draw_requests_async(pool, args.serve_full_requests,
+                                                                  serve_mod.SERVE_SEED, max_pm=None)
 
     import torch
     from paper_2510_16930_gb300 import hoqri
@@ -851,6 +860,19 @@ def run_ours(args):
                              "{4,8,16,32} redrawn while some P_{-n} > 2048, 10 sweeps each, FP32")
             return r
         leg("serve", srv)
+    if side and "serve_full" in legs:
+        def srv_full():
+            import math
+            from paper_2510_16930_gb300 import serve as serve_mod
+            reqs = pending["serve_full"]()
+            r = serve_mod.serve_benchmark(reqs=reqs)
+            r["large_core_requests"] = sum(
+                1 for q, _ in reqs
+                if max(math.prod(q.ranks[:n] + q.ranks[n + 1:]) for n in range(len(q.ranks))) > SERVE_MAX_PM)
+            r["workload"] = ("c5 serving mix without the rank redraw: the first requests of the mix, P_{-n} up to "
+                             "32^3 (the large cores on the column-blocked two-pass kernels), 10 sweeps each, FP32")
+            return r
+        leg("serve_full", srv_full)
     if pool is not None:
         pool.terminate()
     if leg_s:
