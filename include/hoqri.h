@@ -115,7 +115,9 @@ HOQRI_API void hoqri_default_options(hoqri_options *opt);
  *   opt      options (NULL: defaults)
  *   U0       NULL, or N pointers to I_n x K_n reals with orthonormal columns
  *            (not checked); NULL draws a seeded Gaussian and orthonormalises it
- *   stream   cudaStream_t to order all work on (NULL: the legacy default stream)
+ *   stream   cudaStream_t to order all work on (NULL: the legacy default stream;
+ *            on a created stream the context's device memory is allocated
+ *            stream-ordered from the library's pool, see hoqri_trim_memory)
  * Duplicates are summed, then one mode-sorted copy of the nonzeros per mode is
  * built with its permutation and row (slice) descriptors; the raw input is
  * released before returning.  On failure *out is NULL.
