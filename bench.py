@@ -20,7 +20,7 @@ object per further leg (each can be skipped with --legs):
            order sweeps; per-iteration time on the GPU and of the oracle);
   serve    the serving stream (Poisson arrivals of the request mix) through
            the request server against the same requests run one after another
-           as plain contexts;
+           as plain contexts, and latency at 0.5x and 1.2x capacity;
   serve_full (not in the default list) the same on the first --serve-full-requests
            requests of the mix without the P_{-n} <= 2048 redraw, whose large
            cores run on the column-blocked two-pass kernels;
@@ -865,7 +865,7 @@ def run_ours(args):
             import math
             from paper_2510_16930_gb300 import serve as serve_mod
             reqs = pending["serve_full"]()
-            r = serve_mod.serve_benchmark(reqs=reqs)
+            r = serve_mod.serve_benchmark(reqs=reqs, sweep_loads=())
             r["large_core_requests"] = sum(
                 1 for q, _ in reqs
                 if max(math.prod(q.ranks[:n] + q.ranks[n + 1:]) for n in range(len(q.ranks))) > SERVE_MAX_PM)

@@ -134,10 +134,13 @@ SERVE_SEED = 0x484F5152 + 5
 
 
 def serve_benchmark(n_req=2000, seed=SERVE_SEED, budget_bytes=200 << 30, max_active=32, iters=10,
-                    prec=hoqri.HOQRI_FP32, load=0.8, reqs=None, sequential=True):
+                    prec=hoqri.HOQRI_FP32, load=0.8, reqs=None, sequential=True, sweep_loads=(0.5, 1.2),
+                    sweep_requests=500):
     """Capacity from a closed batch (all requests at once), then the open-loop
-    Poisson stream at `load` x that capacity (p50 / p99 latency, nnz/s), and
-    the plain method on the same requests one after another."""
+    Poisson stream at `load` x that capacity (p50 / p99 latency, nnz/s), the
+    plain method on the same requests one after another, and the latency at
+    other loads (`sweep_loads` x capacity) on the first `sweep_requests`
+    requests."""
     if reqs is None:
         reqs = draw_requests(n_req, seed, 1.0, iters)
     n_req = len(reqs)
@@ -165,5 +168,14 @@ def serve_benchmark(n_req=2000, seed=SERVE_SEED, budget_bytes=200 << 30, max_act
         out["resid_differs_from_sequential"] = [
             {"request": k, "served": a, "sequential": b} for k, (a, b) in enumerate(zip(closed["resid"], seq["resid"]))
             if a is not None and a != b][:20]
+    sweep = []
+    sub = reqs[:min(sweep_requests, n_req)]
+    for ld in sweep_loads:
+        r = run_stream(sub, budget_bytes, max_active, prec, iters, arrival_scale=1.0 / (ld * cap_rps))
+        sweep.append({"load": ld, "requests": len(sub), "arrival_rate_req_per_s": ld * cap_rps, "p50_s": r["p50_s"],
+                      "p99_s": r["p99_s"], "nnz_per_s": r["nnz_per_s"], "max_running": r["max_running"],
+                      "failed": len(r["failed"])})
+    if sweep:
+        out["load_sweep"] = sweep
     out["failures"] = dict(list(open_["failed"].items())[:10])
     return out
